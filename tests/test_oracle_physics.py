@@ -1,0 +1,172 @@
+"""Physics pins of the oracle's whole time step (Algorithm 1).
+
+* hydrostatics: a still tank keeps p = rho0 g (H - y) (Sec. 3.4, Eq.
+  p-shepard builds the wall pressure to reproduce it);
+* Taylor-Green vortex: max|u| decays as exp(b t), b = -8 pi^2 / Re (Eq. tgv);
+* pairwise antisymmetry: the "symm" pressure gradient and the viscous force
+  conserve momentum in a periodic box (Eqs. mom:sph:press:symm, mom:sph:visc);
+* GTVF sub-steps: with K = 1 the displacement is dt^2/2 f(r*) exactly, and
+  K sub-steps agree with K = 1 to higher order (Eqs. int:gtvf:pos, :vel:tmp);
+* wall normals of a flat wall point out of the solid (Sec. 3.4.1).
+Planted mistakes in the oracle show that each pin bites.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+RHO0, G = 1000.0, 9.81
+
+
+def _hydro_error(s, c):
+    p = s.get("p"); y = s.get("y"); x = s.get("x")
+    h = c["params"]["h"]
+    H = 20 * 0.05
+    fl = c["kind"] == 0
+    sel = fl & (y > 3 * h) & (y < H - 3 * h) & (x > 3 * h) & (x < 1 - 3 * h)
+    ex = RHO0 * G * (H - y[sel])
+    return np.abs(p[sel] - ex).sum() / np.abs(ex).sum()
+
+
+def test_hydrostatic_tank(oracle_lib):
+    c = workloads.still_tank_2d(20, 20)
+    s = oracle.Sim(c)
+    s.step(1)
+    assert _hydro_error(s, c) < 0.05
+    s.step(49)
+    assert _hydro_error(s, c) < 0.05
+    fl = c["kind"] == 0
+    assert np.abs(s.get("v")[fl]).max() < 0.1 * math.sqrt(2 * G * 1.0)
+
+
+def test_planted_wall_sign_breaks_hydrostatics(oracle_lib):
+    c = workloads.still_tank_2d(20, 20)
+    oracle.plant_mistake(3)
+    try:
+        s = oracle.Sim(c)
+        s.step(1)
+        err = _hydro_error(s, c)
+    finally:
+        oracle.plant_mistake(0)
+    assert err > 0.05
+
+
+def _tgv_run(plant=0, nsteps=10):
+    c = workloads.taylor_green(50)
+    oracle.plant_mistake(plant)
+    try:
+        s = oracle.Sim(c)
+        rc, ds = s.step(nsteps)
+    finally:
+        oracle.plant_mistake(0)
+    t = nsteps * c["params"]["dt"]
+    e0 = np.sum(c["m"] * (c["u"] ** 2 + c["v"] ** 2))
+    e1 = np.sum(c["m"] * (s.get("u") ** 2 + s.get("v") ** 2))
+    # kinetic energy of the exact field decays as exp(2 b t)
+    return c, s, t, math.log(e1 / e0) / (2 * t), ds[-1].umax
+
+
+def test_tgv_decay_rate(oracle_lib):
+    b = -8 * math.pi ** 2 / 100.0
+    c, s, t, rate, umax = _tgv_run()
+    assert abs(rate - b) < 0.05 * abs(b)
+    # max|u| against U exp(b t) with U = 1 (Sec. 4.1 plots exactly this)
+    assert abs(umax - math.exp(b * t)) < 5e-3
+    # L1 error of |u| against the exact field at the particle positions
+    ue, ve, _ = workloads.tgv_exact(s.get("x"), s.get("y"), t)
+    l1 = np.sum(np.abs(np.hypot(s.get("u"), s.get("v")) - np.hypot(ue, ve))) / np.sum(np.hypot(ue, ve))
+    assert l1 < 0.02
+
+
+@pytest.mark.parametrize("plant", [4, 6])
+def test_planted_tgv_mistakes_are_caught(oracle_lib, plant):
+    b = -8 * math.pi ** 2 / 100.0
+    c, s, t, rate, umax = _tgv_run(plant)
+    assert not (abs(rate - b) < 0.05 * abs(b))
+
+
+def _random_periodic(seed):
+    c = workloads.taylor_green(24, perturb=0.25, seed=seed)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    c["rho"] = rng.uniform(0.9, 1.1, c["n"])
+    c["p"] = rng.normal(0, 1, c["n"])
+    c["u"] = rng.normal(0, 1, c["n"])
+    c["v"] = rng.normal(0, 1, c["n"])
+    return c
+
+
+def test_symm_pressure_gradient_conserves_momentum(oracle_lib):
+    c = _random_periodic(21)
+    s = oracle.Sim(c, pgrad_symm=1)
+    s.pressure_gradient()
+    m = c["m"]
+    fx, fy = s.get("fx"), s.get("fy")
+    assert abs(np.sum(m * fx)) < 1e-12 * np.sum(m * np.abs(fx))
+    assert abs(np.sum(m * fy)) < 1e-12 * np.sum(m * np.abs(fy))
+    # the "asymm" form does not conserve momentum for a random field
+    s2 = oracle.Sim(c, pgrad_symm=0)
+    s2.pressure_gradient()
+    assert abs(np.sum(m * s2.get("fx"))) > 1e-6 * np.sum(m * np.abs(s2.get("fx")))
+
+
+def test_viscous_force_conserves_momentum(oracle_lib):
+    c = _random_periodic(22)
+    s = oracle.Sim(c, p_ref=0.0)
+    # transport velocity equal to u switches the artificial stress off
+    s.set("ut", s.get("u")); s.set("vt", s.get("v"))
+    s.stage1()
+    m = c["m"]
+    fx, fy = s.get("fx"), s.get("fy")
+    assert abs(np.sum(m * fx)) < 1e-12 * np.sum(m * np.abs(fx))
+    assert abs(np.sum(m * fy)) < 1e-12 * np.sum(m * np.abs(fy))
+
+
+def test_gtvf_single_substep_closed_form(oracle_lib):
+    c = _random_periodic(23)
+    c["p"] = np.abs(c["p"])
+    s = oracle.Sim(c, gtvf_K=1, pref_mode=2, p_ref=50.0)
+    s.gtvf()
+    dt = c["params"]["dt"]
+    for a, f in (("dx", "fx"), ("dy", "fy")):
+        d, force = s.get(a), s.get(f)
+        assert np.array_equal(d, 0.5 * dt * dt * force)
+    assert np.abs(s.get("fx")).max() > 0
+
+
+def test_gtvf_substeps_agree_to_higher_order(oracle_lib):
+    # With a constant force the K sub-steps give dt^2/2 f for every K; the
+    # force here changes only through the sub-step motion, so the relative
+    # K=4 vs K=1 difference shrinks in proportion to the displacement.
+    c = _random_periodic(24)
+    rel = []
+    for pref in (1.0, 0.1):
+        s1 = oracle.Sim(c, gtvf_K=1, p_ref=pref)
+        s1.gtvf()
+        s4 = oracle.Sim(c, gtvf_K=4, p_ref=pref)
+        s4.gtvf()
+        d1 = np.stack([s1.get("dx"), s1.get("dy")])
+        d4 = np.stack([s4.get("dx"), s4.get("dy")])
+        assert np.abs(d1).max() > 0
+        rel.append(np.abs(d4 - d1).max() / np.abs(d1).max())
+    assert rel[0] < 1e-2
+    assert 0.05 < rel[1] / rel[0] < 0.2
+
+
+def test_flat_wall_normals(oracle_lib):
+    c = workloads.still_tank_2d(12, 12, dx=0.1)
+    s = oracle.Sim(c)
+    nx, ny = s.get("nx"), s.get("ny")
+    x, y = c["x"], c["y"]
+    wall = c["kind"] == 1
+    # first bottom layer away from the corners: normal +y, out of the solid
+    bottom = wall & np.isclose(y, -0.05) & (x > 0.4) & (x < 0.8)
+    assert bottom.sum() > 0
+    assert np.allclose(ny[bottom], 1.0) and np.allclose(nx[bottom], 0.0, atol=1e-12)
+    left = wall & np.isclose(x, -0.05) & (y > 0.4) & (y < 0.8)
+    assert np.allclose(nx[left], 1.0) and np.allclose(ny[left], 0.0, atol=1e-12)
+    assert np.all(nx[~wall] == 0) and np.all(ny[~wall] == 0)
+    mag = np.hypot(nx, ny)
+    assert np.all((np.abs(mag - 1) < 1e-12) | (mag == 0))
