@@ -1,0 +1,371 @@
+"""Benchmark of the SISPH hot path on GB300: one JSON line per run.
+
+A step is one time step of Algorithm 1 (two neighbour searches, density,
+stage-1 forces, PPE set-up, the persistent damped-Jacobi solve to the case's
+tolerance, pressure gradient, GTVF, update) over the whole particle set.
+
+Default workload: the perturbed 400 x 400 Taylor-Green vortex (160,000
+particles, dx = 0.0025, +-0.05 dx seeded noise, Re = 100, h = dx, PPE
+tolerance 1e-4, asymm gradient, p_ref = 100) in the MIXED form (FP32 sums and
+sweeps, FP64 residual and integration), replayed from a CUDA graph.
+Timed steps are bracketed by CUDA events on the library's stream, with a
+256 MiB buffer written between steps to flush the 126 MiB L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload c1|c2|c3|c4|c5] [--precision mixed|fp64]
+
+With N > 1 (torchrun) every rank runs its own replica ("replicas only": one
+case does not shard without a halo exchange); the line reports the total
+particle-steps of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def make_workload(name):
+    """Cases and a description of each benchmark workload."""
+    if name == "c1":
+        return [workloads.taylor_green(50, tol=1e-4)], \
+            "tgv50: 2D Taylor-Green 50x50 lattice, Re 100, tol 1e-4"
+    if name == "c2":
+        return [workloads.taylor_green(400, perturb=0.05, seed=1908, tol=1e-4)], \
+            "tgv400_perturbed: 2D Taylor-Green 400x400, +-0.05dx noise, Re 100, tol 1e-4"
+    if name == "c3":
+        return [workloads.dam_break_2d(dx=0.004)], \
+            "dam_break_2d: 1x2 m column in 4x4 m tank, dx 0.004, 3 wall layers, tol 1e-2"
+    if name == "c4":
+        return [workloads.dam_break_3d(dx=0.008)], \
+            "dam_break_3d: 0.55x1.0x0.55 m column in 1.6x1.0x0.6 m tank, dx 0.008, 3 wall layers"
+    if name == "c5":
+        return workloads.batch_ensemble(64), \
+            "batch64: 32 TGV (Re 50-1000) + 32 cavity (Re 100-1000), n_side 50-300, ~2.5M"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def measured_hbm_peak():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def sweep_bytes(counts_fluid, n_walls_rows, wall_counts, prec_bytes):
+    """Algorithmic bytes of one damped-Jacobi sweep of the stored-coefficient
+    form: per fluid neighbour slot an index and a coefficient; per fluid
+    particle the source, omega/D, the slot count, p^k read and p^{k+1}
+    written; per wall Shepard entry an index and a weight, per wall its count,
+    1/S, H and p_w written.  Neighbour pressures are gathers that the Morton
+    order keeps in cache, so they are not counted."""
+    rb = prec_bytes
+    fluid = np.sum(counts_fluid) * (4 + rb) + counts_fluid.size * (3 * rb + 4 + rb)
+    walls = np.sum(wall_counts) * (4 + rb) + n_walls_rows * (4 + 3 * rb)
+    return float(fluid), float(walls)
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_1908_01762_gb300 import sisph
+    import paper_1908_01762_gb300 as pkg
+
+    if rank == 0:
+        pkg.build()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    dev = torch.device("cuda")
+    cases, desc = make_workload(args.workload)
+    prec = sisph.MIXED if args.precision == "mixed" else sisph.FP64
+    sim = sisph.Simulation(cases, precision=prec, use_graph=1)
+    stream = torch.cuda.current_stream()
+    sisph.sisph_set_stream(sim.h, stream.cuda_stream)
+    n = sim.n
+    kinds = np.concatenate([c["kind"] for c in cases])
+    n_fluid = int(np.sum(kinds == 0))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    # warm-up (also captures the step graph)
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+
+    # time the dominant kernel live, inside the graph-replayed steps
+    sisph.sisph_profile_enable(sim.h, True, "ppe_sweeps")
+    launches0 = sisph.sisph_launch_count(sim.h)
+    it0 = np.array([s.total_iters for s in sim.stats()])
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    counts_hist = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))                 # evict the previous step from L2
+            ev[k][0].record(stream)
+            rc = sim.step(1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    ms_steps = [a.elapsed_time(b) for a, b in ev]
+    t_ms = float(np.sum(ms_steps))
+    launches = sisph.sisph_launch_count(sim.h) - launches0
+    it1 = np.array([s.total_iters for s in sim.stats()])
+    nsw, sweep_ms, _ = sisph.sisph_profile_get(sim.h, "ppe_sweeps")
+    sisph.sisph_profile_enable(sim.h, False)
+    if world > 1:
+        t = torch.tensor([t_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(t.item())
+
+    # algorithmic bytes of the sweep kernel (neighbour lists at the last r*)
+    counts, idx = sisph.sisph_neighbors(sim.h, n)
+    starts = np.concatenate([[0], np.cumsum(counts)])
+    fl = kinds == 0
+    rb = 4 if prec == sisph.MIXED else 8
+    offs = np.cumsum([0] + [c["n"] for c in cases])
+    total_bytes = 0.0
+    pairs = 0.0
+    for ci in range(len(cases)):
+        sl = slice(offs[ci], offs[ci + 1])
+        flc = fl[sl]
+        cnt_c = counts[sl]
+        walls = np.nonzero(~flc)[0] + offs[ci]
+        wall_counts = np.array([np.sum(fl[idx[starts[w]:starts[w + 1]]]) for w in walls]) \
+            if walls.size else np.zeros(0)
+        fb, wb = sweep_bytes(cnt_c[flc], walls.size, wall_counts, rb)
+        its = float(it1[ci] - it0[ci])
+        total_bytes += its * fb + (its + args.steps) * wb
+        pairs += its * float(np.sum(cnt_c[flc]))
+    publish = n * (rb + 8 + (rb if prec == sisph.MIXED else 0))
+    total_bytes += args.steps * publish
+    sweeps = float(np.sum(it1 - it0))
+    iters_per_step = sweeps / args.steps / len(cases)
+    per_launch_bytes = total_bytes / nsw if nsw else 0.0
+    avg_ms = sweep_ms / nsw if nsw else float("nan")
+    achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9 if nsw else None
+    peak, peak_kind = measured_hbm_peak()
+    interactions = pairs
+
+    value = world * n * args.steps / (t_ms * 1e-3)
+    out = {
+        "metric": "particle-steps/s (one SISPH time step of Algorithm 1 per particle)",
+        "value": value,
+        "unit": "particle-steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if prec == sisph.MIXED else "f64",
+        "data": "synthetic",
+        "config": {"workload": desc, "n_particles": n, "n_fluid": n_fluid,
+                   "cases": len(cases), "precision": args.precision,
+                   "ppe_sweeps_per_step": iters_per_step, "l2": "flushed between steps (256 MiB write)",
+                   "graph": "CUDA graph replay per step", "parallelism": f"replicas{world}"},
+        "ppe_interactions_per_s": world * interactions / (t_ms * 1e-3),
+        "roofline": {"kernel": "ppe_sweeps (persistent damped-Jacobi solve)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": None, "peak_source": peak_kind,
+                     "bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms,
+                     "launches": nsw,
+                     "share_of_step": (sweep_ms / t_ms) if t_ms else None},
+        "clocks": clk.summary(),
+        "gpu_launches": int(launches * world),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(cases, args.cpu_seconds)
+    if not args.no_e2e:
+        out["e2e"] = e2e_leg(sim, cases, args, torch, world)
+    sim.close()
+    return out
+
+
+def e2e_leg(sim, cases, args, torch, world):
+    """Same metric through the C-ABI with host buffers: the state lives in
+    pinned host memory; every step copies it to the device (sisph_set),
+    advances one step and reads the whole state back (sisph_get)."""
+    from paper_1908_01762_gb300 import sisph
+    n = sim.n
+    dim = cases[0]["dim"]
+    fields = ["x", "y", "u", "v", "ut", "vt", "p"] + (["z", "w", "wt"] if dim == 3 else [])
+    host = {f: torch.empty(n, dtype=torch.float64, pin_memory=True).numpy() for f in fields}
+    for f in fields:
+        host[f][:] = sim.get(f)
+    steps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for f in fields:
+            sim.set(f, host[f])
+        sim.step(1)
+        for f in fields:
+            sisph.sisph_get(sim.h, f, n, host[f])
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": world * n * steps / dt, "unit": "particle-steps/s",
+            "h2d_bytes_per_step": 8 * n * len(fields), "d2h_bytes_per_step": 8 * n * len(fields),
+            "steps": steps, "timer": "host wall clock, stream synchronised"}
+
+
+def cpu_baseline(cases, seconds):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample."""
+    import oracle
+    oracle.build()
+    c = cases[0]
+    sim = oracle.Sim(c)
+    done, n_tot = 0, 0
+    t0 = time.perf_counter()
+    while True:
+        sim.step(1)
+        done += 1
+        n_tot += c["n"]
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n_tot / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} steps of case 0 ({c['n']} particles) of the same workload, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle (FP64, one core) on the same workload."""
+    import oracle
+    oracle.build()
+    cases, desc = make_workload(args.workload)
+    c = cases[0]
+    sim = oracle.Sim(c)
+    for _ in range(args.warmup):
+        sim.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.step(1)
+    dt = time.perf_counter() - t0
+    n_tot = sum(x["n"] for x in cases)
+    value = c["n"] * args.steps / dt
+    return {
+        "impl": "reference",
+        "metric": "particle-steps/s (one SISPH time step of Algorithm 1 per particle)",
+        "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "n_particles": n_tot, "cases_run": 1,
+                   "precision": "fp64 (oracle)"},
+        "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} steps of case 0 ({c['n']} particles)"},
+        "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, rank, world)))
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,630 @@
+// Neighbour passes of one SISPH time step (Algorithm 1) other than the PPE.
+// One thread per particle, one thread block per tile; every pass reads its
+// neighbours from the ELL lists built by nbr.cu.  Template parameter MX
+// selects the MIXED form: FP32 sums over FP32 cell-relative positions, with
+// the FP64 master state updated in FP64.
+#include "sisph_internal.h"
+
+namespace sisph {
+
+template <int DIM, bool MX>
+struct Geo {
+  using R = typename std::conditional<MX, float, double>::type;
+  double xi[3];
+  float4 pi;
+  __device__ __forceinline__ void init(const State &S, int i) {
+    if constexpr (MX) {
+      pi = S.pf4[i];
+    } else {
+_Pragma("unroll")
+      for (int k = 0; k < DIM; ++k) xi[k] = S.x[k][i];
+    }
+  }
+  __device__ __forceinline__ R pair(const State &S, const CaseDev &P, unsigned e, int &j, R d[3]) const {
+    j = int(e & kIdxMask);
+    if constexpr (MX) {
+      float4 pj = S.pf4[j];
+      return pair_f<DIM>(P, pi, pj, e >> kCodeShift, d);
+    } else {
+      double dd[3];
+      double r2 = pair_d<DIM>(P, xi, S.x, j, dd);
+_Pragma("unroll")
+      for (int k = 0; k < DIM; ++k) d[k] = dd[k];
+      if (DIM == 2) d[2] = 0.0;
+      return r2;
+    }
+  }
+};
+
+template <bool MX>
+__device__ __forceinline__ auto mass(const State &S, int j) {
+  if constexpr (MX) return S.pf4[j].w;
+  else return S.m[j];
+}
+template <bool MX>
+__device__ __forceinline__ auto dens(const State &S, int j) {
+  if constexpr (MX) return S.vf4[j].w;
+  else return S.rho[j];
+}
+template <int DIM, bool MX, typename R>
+__device__ __forceinline__ void vel(const State &S, int j, R u[3]) {
+  if constexpr (MX) {
+    float4 v = S.vf4[j];
+    u[0] = v.x; u[1] = v.y; u[2] = v.z;
+  } else {
+    u[0] = S.u[0][j]; u[1] = S.u[1][j]; u[2] = DIM == 3 ? S.u[2][j] : 0.0;
+  }
+}
+template <int DIM, bool MX, typename R>
+__device__ __forceinline__ void tvel(const State &S, int j, R u[3]) {
+  if constexpr (MX) {
+    float4 v = S.utf4[j];
+    u[0] = v.x; u[1] = v.y; u[2] = v.z;
+  } else {
+    u[0] = S.ut[0][j]; u[1] = S.ut[1][j]; u[2] = DIM == 3 ? S.ut[2][j] : 0.0;
+  }
+}
+
+#define ROW_LOOP(S, i, ...)                                   \
+  {                                                            \
+    const int _cnt = S.ncnt[i];                                \
+    const long long _n = S.n;                                  \
+    for (int _k = 0; _k < _cnt; ++_k) {                        \
+      const unsigned e = S.nbr[(long long)_k * _n + i];        \
+      __VA_ARGS__                                              \
+    }                                                          \
+  }
+
+// ---------------------------------------------------------------------------
+// Summation density, Eq. summation_density, for fluid particles.
+// ---------------------------------------------------------------------------
+template <int DIM, bool MX>
+__global__ void k_density(State S) {
+  using R = typename Geo<DIM, MX>::R;
+  const Tile &t = S.ftiles[blockIdx.x];
+  int i = t.beg + threadIdx.x;
+  if (i >= t.end) return;
+  const CaseDev &P = S.cases[t.c];
+  Geo<DIM, MX> G;
+  G.init(S, i);
+  const R sig = R(P.sig_h), ih = R(P.inv_h);
+  R acc = R(0);
+  ROW_LOOP(S, i, {
+    int j;
+    R d[3];
+    R r2 = G.pair(S, P, e, j, d);
+    acc += mass<MX>(S, j) * sig * poly_w<R>(qof<R>(sqrt_r(r2), P.h, P.inv_h));
+  })
+  S.rho[i] = double(acc);
+  if constexpr (MX) S.vf4[i].w = float(acc);
+}
+
+// ---------------------------------------------------------------------------
+// Wall normals, Sec. 3.4.1 (computed once; walls never move), FP64:
+//   n*_i = -sum_j (m_j/rho_j) grad W_ij over wall neighbours, zero if
+//   |n*| < 1/(4h) else unit; n_i = sum_j (m_j/rho_j) n*_j W_ij, unit, or zero
+//   when shorter than 1e-6 (a cancelled average of unit vectors).
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void k_normals(State S, int pass) {
+  const Tile &t = S.wtiles[blockIdx.x];
+  int i = t.beg + threadIdx.x;
+  if (i >= t.end) return;
+  const CaseDev &P = S.cases[t.c];
+  double xi[3] = {S.x[0][i], S.x[1][i], DIM == 3 ? S.x[2][i] : 0.0};
+  double acc[3] = {0, 0, 0};
+  const int wend = P.wbeg + P.nw;
+  ROW_LOOP(S, i, {
+    int j = int(e & kIdxMask);
+    if (j >= P.wbeg && j < wend) {
+      double d[3] = {0, 0, 0};
+      double r2 = pair_d<DIM>(P, xi, S.x, j, d);
+      double r = sqrt(r2);
+      double vj = S.m[j] / S.rho[j];
+      if (pass == 0) {
+        double fr = r > 0.0 ? P.sig_h * P.inv_h * poly_dw<double>(r / P.h) / r : 0.0;
+_Pragma("unroll")
+        for (int k = 0; k < DIM; ++k) acc[k] -= vj * fr * d[k];
+      } else {
+        double w = vj * P.sig_h * poly_w<double>(r / P.h);
+_Pragma("unroll")
+        for (int k = 0; k < DIM; ++k) acc[k] += w * S.nstar[k][j];
+      }
+    }
+  })
+  double mag = sqrt(acc[0] * acc[0] + acc[1] * acc[1] + acc[2] * acc[2]);
+  double thr = pass == 0 ? 1.0 / (4.0 * P.h) : 1e-6;
+  bool keep = pass == 0 ? !(mag < thr) : (mag > thr);
+_Pragma("unroll")
+  for (int k = 0; k < 3; ++k) {
+    double v = keep ? acc[k] / mag : 0.0;
+    if (pass == 0) S.nstar[k][i] = v;
+    else S.nrm[k][i] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Wall ghost velocity, Sec. 3.4, Eqs. vf, vg-adami, vg-no-normal.
+//  no-slip (stage 1): u~ = Shepard(u_f, h/2), u_w = 2 u_wall - u~, and the
+//    component into the solid removed;  u~ = u_wall without fluid in range.
+//  slip (stage 2, u* of the PPE source): u_w = Shepard(u*_f, h), the fluid's
+//    own u* extended into the wall (u_wall without fluid in range).
+// The result is written into the wall's velocity slot.
+// ---------------------------------------------------------------------------
+template <int DIM, bool MX>
+__global__ void k_ghost(State S, int slip_stage) {
+  using R = typename Geo<DIM, MX>::R;
+  const Tile &t = S.wtiles[blockIdx.x];
+  int i = t.beg + threadIdx.x;
+  if (i >= t.end) return;
+  const CaseDev &P = S.cases[t.c];
+  const bool slip = slip_stage && P.ustar_slip;
+  const R sig = R(slip ? P.sig_h : P.sig_h2);
+  const double hk = slip ? P.h : P.h2, ih = slip ? P.inv_h : P.inv_h2;
+  Geo<DIM, MX> G;
+  G.init(S, i);
+  R sw = R(0), su[3] = {R(0), R(0), R(0)};
+  const int fend = P.fbeg + P.nf;
+  ROW_LOOP(S, i, {
+    int j = int(e & kIdxMask);
+    if (j < fend) {
+      R d[3];
+      R r2 = G.pair(S, P, e, j, d);
+      R w = sig * poly_w<R>(qof<R>(sqrt_r(r2), hk, ih));
+      R uj[3];
+      vel<DIM, MX>(S, j, uj);
+      sw += w;
+_Pragma("unroll")
+      for (int k = 0; k < DIM; ++k) su[k] += uj[k] * w;
+    }
+  })
+  double ug[3] = {0, 0, 0}, nn[3] = {0, 0, 0}, ut[3];
+_Pragma("unroll")
+  for (int k = 0; k < DIM; ++k) {
+    ut[k] = sw > R(0) ? double(su[k]) / double(sw) : S.uw[k][i];
+    nn[k] = S.nrm[k][i];
+  }
+  if (slip) {
+_Pragma("unroll")
+    for (int k = 0; k < DIM; ++k) ug[k] = ut[k];
+  } else {
+_Pragma("unroll")
+    for (int k = 0; k < DIM; ++k) ug[k] = 2.0 * S.uw[k][i] - ut[k];
+    double un = ug[0] * nn[0] + ug[1] * nn[1] + ug[2] * nn[2];
+    if (un < 0.0) {
+_Pragma("unroll")
+      for (int k = 0; k < DIM; ++k) ug[k] -= un * nn[k];
+    }
+  }
+_Pragma("unroll")
+  for (int k = 0; k < DIM; ++k) S.u[k][i] = ug[k];
+  if constexpr (MX) {
+    float4 v = S.vf4[i];
+    v.x = float(ug[0]); v.y = float(ug[1]); v.z = float(ug[2]);
+    S.vf4[i] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stage 1, Eqs. int:rnp1 and int:vint:  r* = r^n + dt u~^n,
+// u* = u^n + dt (f_visc + f_avisc + f_astress + g) with
+//   f_visc   = sum_j m_j 4 nu/(rho_i+rho_j) (r_ij.gradW)/(r^2+eta h^2) u_ij
+//   f_avisc  = -sum_j m_j Pi_ij gradW, Pi_ij = -alpha h c phi_ij/rho_bar for
+//              u_ij.r_ij < 0, phi_ij = u_ij.r_ij/(r^2+eta h^2)
+//   f_astress= sum_{j fluid} m_j (A_i/rho_i^2 + A_j/rho_j^2).gradW,
+//              A = rho u (x) (u~ - u)
+// Walls enter with their ghost velocity.  Writes r*, u* to the stage-1
+// buffers (neighbours still read r^n, u^n).
+// ---------------------------------------------------------------------------
+template <int DIM, bool MX>
+__global__ void k_stage1(State S) {
+  using R = typename Geo<DIM, MX>::R;
+  const Tile &t = S.ftiles[blockIdx.x];
+  int i = t.beg + threadIdx.x;
+  if (i >= t.end) return;
+  const CaseDev &P = S.cases[t.c];
+  Geo<DIM, MX> G;
+  G.init(S, i);
+  const R sig = R(P.sig_h), ih = R(P.inv_h);
+  const R dsc = sig * ih;
+  const R nu4 = R(4.0 * P.nu), eh2 = R(P.eh2);
+  const R avc = R(P.alpha * P.h * P.c0);
+  const bool av = P.alpha > 0.0;
+  const int fend = P.fbeg + P.nf;
+  R ui[3], uti[3];
+  vel<DIM, MX>(S, i, ui);
+  tvel<DIM, MX>(S, i, uti);
+  const R ri = dens<MX>(S, i);
+  R dti[3];
+_Pragma("unroll")
+  for (int k = 0; k < 3; ++k) dti[k] = uti[k] - ui[k];
+  R f[3] = {R(0), R(0), R(0)};
+  ROW_LOOP(S, i, {
+    int j;
+    R d[3];
+    R r2 = G.pair(S, P, e, j, d);
+    if (j != i) {
+      R r = sqrt_r(r2);
+      R dw = dsc * poly_dw<R>(qof<R>(r, P.h, P.inv_h));
+      R fr = r > R(0) ? dw / r : R(0);
+      R rj = dens<MX>(S, j), mj = mass<MX>(S, j);
+      R uj[3];
+      vel<DIM, MX>(S, j, uj);
+      R uij[3] = {ui[0] - uj[0], ui[1] - uj[1], ui[2] - uj[2]};
+      R rdw = fr * r2;
+      R visc = mj * nu4 / (ri + rj) * rdw / (r2 + eh2);
+      R coef = R(0);
+      if (av) {
+        R vr = uij[0] * d[0] + uij[1] * d[1] + (DIM == 3 ? uij[2] * d[2] : R(0));
+        if (vr < R(0)) {
+          R phi = vr / (r2 + eh2);
+          R pij = -avc * phi / (R(0.5) * (ri + rj));
+          coef -= mj * pij;
+        }
+      }
+      R ai = R(0), aj = R(0);
+      if (j < fend) {
+        R utj[3];
+        tvel<DIM, MX>(S, j, utj);
+        R gi = R(0), gj = R(0);
+_Pragma("unroll")
+        for (int k = 0; k < DIM; ++k) {
+          gi += dti[k] * d[k];
+          gj += (utj[k] - uj[k]) * d[k];
+        }
+        ai = mj * fr * gi / ri;
+        aj = mj * fr * gj / rj;
+      }
+_Pragma("unroll")
+      for (int k = 0; k < DIM; ++k)
+        f[k] += visc * uij[k] + coef * fr * d[k] + ui[k] * ai + uj[k] * aj;
+    }
+  })
+  const double dt = P.dt;
+_Pragma("unroll")
+  for (int k = 0; k < DIM; ++k) {
+    double fk = double(f[k]) + P.g[k];
+    S.us[k][i] = S.u[k][i] + dt * fk;
+    double xk = __dadd_rn(S.x[k][i], __dmul_rn(dt, S.ut[k][i]));
+    if (P.per[k]) {
+      if (xk >= P.hi[k]) xk -= P.L[k];
+      else if (xk < P.lo[k]) xk += P.L[k];
+    }
+    S.xs[k][i] = xk;
+  }
+}
+
+// Walls do not move: their stage-1 outputs are their current state.
+template <int DIM>
+__global__ void k_stage1_walls(State S) {
+  const Tile &t = S.wtiles[blockIdx.x];
+  int i = t.beg + threadIdx.x;
+  if (i >= t.end) return;
+_Pragma("unroll")
+  for (int k = 0; k < DIM; ++k) {
+    S.xs[k][i] = S.x[k][i];
+    S.us[k][i] = S.u[k][i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pressure gradient and correction, Eqs. mom:sph:press:symm / :pij, int:vnp1:
+//   symm : f_p = -sum_j m_j (p_i/rho_i^2 + p_j/rho_j^2) gradW
+//   asymm: f_p = -sum_j m_j/(rho_i rho_j) (p_j - p_i) gradW
+//   u^{n+1} = u* + dt f_p
+// ---------------------------------------------------------------------------
+template <int DIM, bool MX>
+__global__ void k_pgrad(State S) {
+  using R = typename Geo<DIM, MX>::R;
+  const Tile &t = S.ftiles[blockIdx.x];
+  int i = t.beg + threadIdx.x;
+  if (i >= t.end) return;
+  const CaseDev &P = S.cases[t.c];
+  Geo<DIM, MX> G;
+  G.init(S, i);
+  const R dsc = R(P.sig_h * P.inv_h), ih = R(P.inv_h);
+  const R ri = dens<MX>(S, i);
+  R pi;
+  if constexpr (MX) pi = S.pf[i];
+  else pi = S.p[i];
+  const R pri = pi / (ri * ri);
+  R f[3] = {R(0), R(0), R(0)};
+  const bool symm = P.pgrad_symm != 0;
+  ROW_LOOP(S, i, {
+    int j;
+    R d[3];
+    R r2 = G.pair(S, P, e, j, d);
+    if (j != i) {
+      R r = sqrt_r(r2);
+      R fr = r > R(0) ? dsc * poly_dw<R>(qof<R>(r, P.h, P.inv_h)) / r : R(0);
+      R rj = dens<MX>(S, j), mj = mass<MX>(S, j);
+      R pj;
+      if constexpr (MX) pj = S.pf[j];
+      else pj = S.p[j];
+      R c = symm ? -mj * (pri + pj / (rj * rj)) : -mj / (ri * rj) * (pj - pi);
+      c *= fr;
+_Pragma("unroll")
+      for (int k = 0; k < DIM; ++k) f[k] += c * d[k];
+    }
+  })
+_Pragma("unroll")
+  for (int k = 0; k < DIM; ++k) S.u[k][i] = S.u[k][i] + P.dt * double(f[k]);
+}
+
+// p_ref = 2 max_i p_i after the first PPE solve (internal flows, Sec. 2.1);
+// one block per case, only while the case's flag is unset.
+__global__ void k_pref(State S) {
+  int c = blockIdx.x;
+  const CaseDev &P = S.cases[c];
+  if (P.pref_mode != SISPH_PREF_TWICE_MAX_FIRST || S.pref_set[c]) return;
+  double mx = -1e300;
+  for (int i = P.fbeg + threadIdx.x; i < P.fbeg + P.nf; i += blockDim.x) mx = fmax(mx, S.p[i]);
+  __shared__ double sh[32];
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = sh[0];
+    for (int w = 1; w < int(blockDim.x >> 5); ++w) m = fmax(m, sh[w]);
+    S.pref[c] = P.nf > 0 ? 2.0 * m : 0.0;
+    S.pref_set[c] = 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// GTVF homogenisation, Eqs. mom:sph:gtvf, int:gtvf:pos, int:gtvf:vel:tmp:
+//   f_i = -p0_i sum_j (m_j/rho_j^2) grad W(r_ij, h~), on the r* lists with
+//   distances from the sub-step positions (r* + d), d^0 = 0, u~^0 = 0;
+//   d^k = d^{k-1} + dtau u~^{k-1} + dtau^2/2 f,  u~^k = u~^{k-1} + dtau f.
+//   p0_i = p_ref, or min(10|p_i|, p_ref) for external flows.
+// ---------------------------------------------------------------------------
+template <int DIM, bool MX>
+__global__ void k_gtvf(State S, int sub, int cur) {
+  using R = typename Geo<DIM, MX>::R;
+  const Tile &t = S.ftiles[blockIdx.x];
+  int i = t.beg + threadIdx.x;
+  if (i >= t.end) return;
+  const CaseDev &P = S.cases[t.c];
+  if (sub >= P.K) return;
+  Geo<DIM, MX> G;
+  G.init(S, i);
+  const R dsc = R(P.sig_hg * P.inv_hg), ih = R(P.inv_hg);
+  const int fend = P.fbeg + P.nf;
+  R di[3] = {R(0), R(0), R(0)};
+  if (sub > 0) {
+    if constexpr (MX) {
+      float4 v = S.dgf[cur][i];
+      di[0] = v.x; di[1] = v.y; di[2] = v.z;
+    } else {
+_Pragma("unroll")
+      for (int k = 0; k < DIM; ++k) di[k] = S.dg[cur][k][i];
+    }
+  }
+  R acc[3] = {R(0), R(0), R(0)};
+  ROW_LOOP(S, i, {
+    int j;
+    R d[3];
+    G.pair(S, P, e, j, d);
+    if (j != i) {
+      if (sub > 0 && j < fend) {
+        R dj[3];
+        if constexpr (MX) {
+          float4 v = S.dgf[cur][j];
+          dj[0] = v.x; dj[1] = v.y; dj[2] = v.z;
+        } else {
+_Pragma("unroll")
+          for (int k = 0; k < DIM; ++k) dj[k] = S.dg[cur][k][j];
+        }
+_Pragma("unroll")
+        for (int k = 0; k < DIM; ++k) d[k] += di[k] - dj[k];
+      }
+      R r2 = d[0] * d[0] + d[1] * d[1] + (DIM == 3 ? d[2] * d[2] : R(0));
+      R r = sqrt_r(r2);
+      if (r > R(0)) {
+        R fr = dsc * poly_dw<R>(qof<R>(r, P.hg, P.inv_hg)) / r;
+        R rj = dens<MX>(S, j);
+        R c = mass<MX>(S, j) / (rj * rj) * fr;
+_Pragma("unroll")
+        for (int k = 0; k < DIM; ++k) acc[k] += c * d[k];
+      }
+    }
+  })
+  double pref = S.pref[t.c];
+  double pi = S.p[i];
+  double p0 = P.pref_mode == SISPH_PREF_EXTERNAL ? fmin(10.0 * fabs(pi), pref) : pref;
+  const double dtau = P.dt / P.K;
+  const int nxt = cur ^ 1;
+  double dn[3] = {0, 0, 0};
+_Pragma("unroll")
+  for (int k = 0; k < DIM; ++k) {
+    double fk = -p0 * double(acc[k]);
+    double vk = sub > 0 ? S.vgt[k][i] : 0.0;
+    double dk = sub > 0 ? double(di[k]) : 0.0;
+    if constexpr (!MX) dk = sub > 0 ? S.dg[cur][k][i] : 0.0;
+    dn[k] = dk + dtau * vk + 0.5 * dtau * dtau * fk;
+    S.vgt[k][i] = vk + dtau * fk;
+    if constexpr (!MX) S.dg[nxt][k][i] = dn[k];
+  }
+  if constexpr (MX) S.dgf[nxt][i] = make_float4(float(dn[0]), float(dn[1]), float(dn[2]), 0.f);
+}
+
+// ---------------------------------------------------------------------------
+// Eqs. int:vhatnp2, int:rnp2:  u~^{n+1} = u^{n+1} + (r^K - r^0)/dt,
+//   r^{n+1} = r^n + dt (u~^{n+1} + u~^n)/2, wrapped into periodic boxes.
+// ---------------------------------------------------------------------------
+template <int DIM, bool MX>
+__global__ void k_update(State S, int fin) {
+  const Tile &t = S.ftiles[blockIdx.x];
+  int i = t.beg + threadIdx.x;
+  if (i >= t.end) return;
+  const CaseDev &P = S.cases[t.c];
+  const int par = P.K > 0 ? (P.K & 1) : 0;
+  (void)fin;
+  const double dt = P.dt;
+  float4 df = make_float4(0.f, 0.f, 0.f, 0.f);
+  if constexpr (MX) df = S.dgf[par][i];
+  const float dfa[3] = {df.x, df.y, df.z};
+_Pragma("unroll")
+  for (int k = 0; k < DIM; ++k) {
+    double dk;
+    if constexpr (MX) dk = double(dfa[k]);
+    else dk = S.dg[par][k][i];
+    double old = S.ut[k][i];
+    double nw = __dadd_rn(S.u[k][i], __ddiv_rn(dk, dt));
+    double xk = __dadd_rn(S.xn[k][i], __dmul_rn(__dmul_rn(0.5, dt), __dadd_rn(nw, old)));
+    if (P.per[k]) {
+      if (xk >= P.hi[k]) xk -= P.L[k];
+      else if (xk < P.lo[k]) xk += P.L[k];
+    }
+    S.x[k][i] = xk;
+    S.ut[k][i] = nw;
+  }
+}
+
+// Refresh the FP32 mirrors of velocity / density / pressure (MIXED) after
+// the FP64 master state was written from the host.
+__global__ void k_refresh(State S) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S.n) return;
+  double u2 = S.dim == 3 ? S.u[2][i] : 0.0, t2 = S.dim == 3 ? S.ut[2][i] : 0.0;
+  S.vf4[i] = make_float4(float(S.u[0][i]), float(S.u[1][i]), float(u2), float(S.rho[i]));
+  S.utf4[i] = make_float4(float(S.ut[0][i]), float(S.ut[1][i]), float(t2), 0.f);
+  S.pf[i] = float(S.p[i]);
+}
+
+// out_user[uid[i]] = field[i]
+__global__ void k_scatter_field(State S, const void *src, int is_float, int stride_f4, int comp,
+                                double *dst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S.n) return;
+  double v;
+  if (stride_f4) v = double((&static_cast<const float4 *>(src)[i].x)[comp]);
+  else if (is_float) v = double(static_cast<const float *>(src)[i]);
+  else v = static_cast<const double *>(src)[i];
+  dst[S.uid[i]] = v;
+}
+
+__global__ void k_gather_field(State S, const double *src, double *dst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S.n) return;
+  dst[i] = src[S.uid[i]];
+}
+
+// ---------------------------------------------------------------------------
+#define DISPATCH(S, KERN, ...)                                    \
+  do {                                                            \
+    if (S.dim == 2) {                                             \
+      if (S.mixed) KERN<2, true> __VA_ARGS__;                     \
+      else KERN<2, false> __VA_ARGS__;                            \
+    } else {                                                      \
+      if (S.mixed) KERN<3, true> __VA_ARGS__;                     \
+      else KERN<3, false> __VA_ARGS__;                            \
+    }                                                             \
+  } while (0)
+
+cudaError_t launch_density(const State &S, const Launch &L) {
+  if (S.nft == 0) return cudaSuccess;
+  if (L.before) L.before(L.ctx, "density");
+  DISPATCH(S, k_density, <<<S.nft, S.T, 0, L.stream>>>(S));
+  if (L.after) L.after(L.ctx, "density", double(S.nf), 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normals(const State &S, const Launch &L) {
+  if (S.nwt == 0) return cudaSuccess;
+  for (int pass = 0; pass < 2; ++pass) {
+    if (S.dim == 2) k_normals<2><<<S.nwt, S.T, 0, L.stream>>>(S, pass);
+    else k_normals<3><<<S.nwt, S.T, 0, L.stream>>>(S, pass);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ghost(const State &S, const Launch &L, int slip_stage) {
+  if (S.nwt == 0) return cudaSuccess;
+  if (L.before) L.before(L.ctx, "ghost");
+  DISPATCH(S, k_ghost, <<<S.nwt, S.T, 0, L.stream>>>(S, slip_stage));
+  if (L.after) L.after(L.ctx, "ghost", double(S.nw), 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stage1(const State &S, const Launch &L) {
+  if (L.before) L.before(L.ctx, "stage1");
+  if (S.nft) DISPATCH(S, k_stage1, <<<S.nft, S.T, 0, L.stream>>>(S));
+  if (S.nwt) {
+    if (S.dim == 2) k_stage1_walls<2><<<S.nwt, S.T, 0, L.stream>>>(S);
+    else k_stage1_walls<3><<<S.nwt, S.T, 0, L.stream>>>(S);
+  }
+  if (L.after) L.after(L.ctx, "stage1", double(S.nf), (S.nft ? 1 : 0) + (S.nwt ? 1 : 0));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pgrad(const State &S, const Launch &L) {
+  if (S.nft == 0) return cudaSuccess;
+  if (L.before) L.before(L.ctx, "pgrad");
+  DISPATCH(S, k_pgrad, <<<S.nft, S.T, 0, L.stream>>>(S));
+  if (L.after) L.after(L.ctx, "pgrad", double(S.nf), 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pref(const State &S, const Launch &L) {
+  if (L.before) L.before(L.ctx, "pref");
+  k_pref<<<S.ncases, 256, 0, L.stream>>>(S);
+  if (L.after) L.after(L.ctx, "pref", double(S.ncases), 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gtvf(const State &S, const Launch &L, int kmax) {
+  if (S.nft == 0) return cudaSuccess;
+  if (L.before) L.before(L.ctx, "gtvf");
+  for (int sub = 0; sub < kmax; ++sub) DISPATCH(S, k_gtvf, <<<S.nft, S.T, 0, L.stream>>>(S, sub, sub & 1));
+  if (L.after) L.after(L.ctx, "gtvf", double(S.nf) * kmax, kmax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(const State &S, const Launch &L) {
+  if (S.nft == 0) return cudaSuccess;
+  if (L.before) L.before(L.ctx, "update");
+  DISPATCH(S, k_update, <<<S.nft, S.T, 0, L.stream>>>(S, 0));
+  if (L.after) L.after(L.ctx, "update", double(S.nf), 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refresh_mirrors(const State &S, const Launch &L) {
+  if (!S.mixed) return cudaSuccess;
+  k_refresh<<<(S.n + 255) / 256, 256, 0, L.stream>>>(S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_field(const State &S, const Launch &L, const void *src, int is_float,
+                                 int stride_f4, int comp, double *dst_user) {
+  k_scatter_field<<<(S.n + 255) / 256, 256, 0, L.stream>>>(S, src, is_float, stride_f4, comp, dst_user);
+  return cudaGetLastError();
+}
+
+// Final GTVF displacement (buffer K & 1 of each particle's case) in user order.
+__global__ void k_scatter_disp(State S, int comp, double *dst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S.n) return;
+  int c = S.case_of[i];
+  const CaseDev &P = S.cases[c];
+  double v = 0.0;
+  bool fluid = i < P.fbeg + P.nf;
+  if (fluid && comp < S.dim) {
+    int par = P.K & 1;
+    if (S.mixed) v = double((&S.dgf[par][i].x)[comp]);
+    else v = S.dg[par][comp][i];
+  }
+  dst[S.uid[i]] = v;
+}
+
+cudaError_t launch_scatter_disp(const State &S, const Launch &L, int comp, double *dst_user) {
+  k_scatter_disp<<<(S.n + 255) / 256, 256, 0, L.stream>>>(S, comp, dst_user);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_field(const State &S, const Launch &L, const double *src_user, double *dst) {
+  k_gather_field<<<(S.n + 255) / 256, 256, 0, L.stream>>>(S, src_user, dst);
+  return cudaGetLastError();
+}
+
+}  // namespace sisph

@@ -1,0 +1,453 @@
+// Pressure-Poisson solve of SISPH (Sec. 3): set-up of the source term and of
+// the per-pair coefficients (Eqs. sph-ppe, iterative-p, coeff, coeff1), the
+// wall-pressure rows of Eq. p-shepard, and one persistent kernel that runs
+// every damped-Jacobi sweep (Eq. p-sor) with its wall extrapolation and the
+// FP64 convergence test of Eq. convergence for all cases at once.
+//
+// Coefficients are stored for the duration of one solve (one number per
+// neighbour slot) so that each sweep streams coefficients instead of
+// recomputing the kernel gradient; there is still no global matrix assembly.
+#include <cooperative_groups.h>
+
+#include "sisph_internal.h"
+
+namespace sisph {
+
+template <typename R>
+__device__ __forceinline__ void kahan_add(R &sum, R &comp, R v) {
+  R y = v - comp;
+  R t = sum + y;
+  comp = (t - sum) - y;
+  sum = t;
+}
+
+// ---------------------------------------------------------------------------
+// Fluid set-up: RHS_i = sum_j -(m_j/(rho_j dt)) u*_ij . grad_i W_ij and
+// fac_ij = 4 m_j/(rho_i (rho_i+rho_j)) (r_ij . grad_i W_ij)/(r^2 + eta h^2),
+// D_ii = sum_j fac_ij (Kahan-compensated in FP32 for the MIXED form).  A
+// particle with D_ii = 0 or on the free surface (rho_i/rho0 < fs_ratio) is
+// inactive: p = 0 for the whole solve.  Lambda = max |RHS_i/D_ii| per tile.
+// ---------------------------------------------------------------------------
+template <int DIM, bool MX>
+__global__ void k_setup_fluid(State S) {
+  using R = typename std::conditional<MX, float, double>::type;
+  const Tile &t = S.ftiles[blockIdx.x];
+  int i = t.beg + threadIdx.x;
+  const CaseDev &P = S.cases[t.c];
+  double lam = 0.0;
+  if (i < t.end) {
+    double xi[3] = {0, 0, 0};
+    float4 pi4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    R ri, ui[3];
+    if constexpr (MX) {
+      pi4 = S.pf4[i];
+      float4 v = S.vf4[i];
+      ri = v.w; ui[0] = v.x; ui[1] = v.y; ui[2] = v.z;
+    } else {
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) { xi[k] = S.x[k][i]; ui[k] = S.u[k][i]; }
+      if (DIM == 2) ui[2] = 0.0;
+      ri = S.rho[i];
+    }
+    const R dsc = R(P.sig_h * P.inv_h), ih = R(P.inv_h), eh2 = R(P.eh2);
+    const R idt = R(1.0 / P.dt);
+    R rhs = R(0), rc = R(0), dg = R(0), dc = R(0);
+    const int cnt = S.ncnt[i];
+    const long long n = S.n;
+    R *coef = static_cast<R *>(S.coef);
+    for (int k = 0; k < cnt; ++k) {
+      unsigned e = S.nbr[(long long)k * n + i];
+      int j = int(e & kIdxMask);
+      R fac = R(0);
+      if (j != i) {
+        R d[3], r2, rj, mj, uj[3];
+        if constexpr (MX) {
+          float4 pj = S.pf4[j];
+          r2 = pair_f<DIM>(P, pi4, pj, e >> kCodeShift, d);
+          float4 v = S.vf4[j];
+          rj = v.w; uj[0] = v.x; uj[1] = v.y; uj[2] = v.z;
+          mj = pj.w;
+        } else {
+          double dd[3];
+          r2 = pair_d<DIM>(P, xi, S.x, j, dd);
+#pragma unroll
+          for (int q = 0; q < DIM; ++q) { d[q] = dd[q]; uj[q] = S.u[q][j]; }
+          if (DIM == 2) { d[2] = 0.0; uj[2] = 0.0; }
+          rj = S.rho[j];
+          mj = S.m[j];
+        }
+        R r = sqrt_r(r2);
+        R fr = r > R(0) ? dsc * poly_dw<R>(qof<R>(r, P.h, P.inv_h)) / r : R(0);
+        R ud = R(0);
+#pragma unroll
+        for (int q = 0; q < DIM; ++q) ud += (ui[q] - uj[q]) * d[q];
+        R src = -(mj / rj) * idt * fr * ud;
+        fac = R(4) * mj / (ri * (ri + rj)) * (fr * r2) / (r2 + eh2);
+        if constexpr (MX) {
+          kahan_add(rhs, rc, src);
+          kahan_add(dg, dc, fac);
+        } else {
+          rhs += src;
+          dg += fac;
+        }
+      }
+      coef[(long long)k * n + i] = fac;
+    }
+    bool fs = P.free_surface && (double(ri) / P.rho0 < S.fs_ratio);
+    bool active = (dg != R(0)) && !fs;
+    static_cast<R *>(S.prhs)[i] = active ? rhs : R(0);
+    static_cast<R *>(S.pwd)[i] = active ? R(S.omega) / dg : R(0);
+    S.rhs_out[i] = double(rhs);
+    S.diag_out[i] = double(dg);
+    double p0 = active ? (MX ? double(S.pf[i]) : S.p[i]) : 0.0;
+    static_cast<R *>(S.pb[0])[i] = R(p0);
+    if (!active) {
+      S.p[i] = 0.0;
+      if constexpr (MX) S.pf[i] = 0.f;
+    }
+    if (active) lam = fabs(double(rhs) / double(dg));
+  }
+  __shared__ double sh[32];
+  for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = lam;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = sh[0];
+    for (int w = 1; w < int(blockDim.x >> 5); ++w) m = fmax(m, sh[w]);
+    S.tile_lam[blockIdx.x] = m;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Wall set-up for Eq. p-shepard: for wall w the fluid neighbours f, W_wf,
+// 1/sum_f W_wf and H_w = (g - a_w) . sum_f rho_f r_wf W_wf (a_w = 0,
+// r_wf = r_w - r_f), stored as compact rows so that a sweep only streams
+// fluid entries.
+// ---------------------------------------------------------------------------
+template <int DIM, bool MX>
+__global__ void k_setup_wall(State S) {
+  using R = typename std::conditional<MX, float, double>::type;
+  const Tile &t = S.wtiles[blockIdx.x];
+  int i = t.beg + threadIdx.x;
+  if (i >= t.end) return;
+  const CaseDev &P = S.cases[t.c];
+  const int r = P.wrow + (i - P.wbeg);
+  const int fend = P.fbeg + P.nf;
+  double xi[3] = {0, 0, 0};
+  float4 pi4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  if constexpr (MX) pi4 = S.pf4[i];
+  else {
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) xi[k] = S.x[k][i];
+  }
+  const R sig = R(P.sig_h), ih = R(P.inv_h);
+  R sw = R(0), acc[3] = {R(0), R(0), R(0)};
+  int cnt = 0;
+  const int cnti = S.ncnt[i];
+  const long long n = S.n, nw = S.nw;
+  R *wc = static_cast<R *>(S.wcoef);
+  for (int k = 0; k < cnti; ++k) {
+    unsigned e = S.nbr[(long long)k * n + i];
+    int j = int(e & kIdxMask);
+    if (j >= fend) continue;
+    R d[3], r2, rj;
+    if constexpr (MX) {
+      float4 pj = S.pf4[j];
+      r2 = pair_f<DIM>(P, pi4, pj, e >> kCodeShift, d);
+      rj = S.vf4[j].w;
+    } else {
+      double dd[3];
+      r2 = pair_d<DIM>(P, xi, S.x, j, dd);
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) d[q] = dd[q];
+      if (DIM == 2) d[2] = 0.0;
+      rj = S.rho[j];
+    }
+    R w = sig * poly_w<R>(qof<R>(sqrt_r(r2), P.h, P.inv_h));
+    S.widx[(long long)cnt * nw + r] = j;
+    wc[(long long)cnt * nw + r] = w;
+    ++cnt;
+    sw += w;
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) acc[q] += rj * d[q] * w;
+  }
+  R hw = R(0);
+#pragma unroll
+  for (int q = 0; q < DIM; ++q) hw += R(P.g[q]) * acc[q];
+  S.wcnt[r] = cnt;
+  static_cast<R *>(S.wsinv)[r] = sw > R(0) ? R(1) / sw : R(0);
+  static_cast<R *>(S.wh)[r] = hw;
+}
+
+// ---------------------------------------------------------------------------
+// Grid barrier with a bounded wait.  All blocks are co-resident (cooperative
+// launch).  A wait that exceeds `budget` clock cycles, or that sees another
+// block's error, marks the error word and returns false; the caller returns.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool grid_sync(Barrier *b, unsigned nblocks, long long budget, bool skip_arrive) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned *vgen = &b->gen;
+    volatile int *verr = &b->err;
+    unsigned g = *vgen;
+    __threadfence();
+    bool last = false;
+    if (!skip_arrive) last = (atomicAdd(&b->count, 1u) == nblocks - 1);
+    if (last) {
+      b->count = 0;
+      __threadfence();
+      atomicExch(&b->gen, g + 1u);
+    } else {
+      long long t0 = clock64();
+      while (*vgen == g) {
+        if (*verr) { ok = 0; break; }
+        if (clock64() - t0 > budget) {
+          atomicExch(&b->err, kErrTimeout);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__device__ __forceinline__ void block_sum2(double &a, double &b, double *sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) { sh[w] = a; sh[32 + w] = b; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int q = 0; q < nw; ++q) { sa += sh[q]; sb += sh[32 + q]; }
+    a = sa;
+    b = sb;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent damped-Jacobi solve for all cases.  Iteration k:
+//   W phase: each case's owner block decides from the partial sums of
+//     sweep k-1 whether the case goes on (Eq. convergence; at least
+//     min_iter sweeps, at most max_iter); every case that swept last time
+//     extrapolates its wall pressure from p^k (Eq. p-shepard, clamped at 0
+//     for free-surface flows) -- for a finished case this is the final
+//     wall update;
+//   barrier;
+//   F phase: p^{k+1}_i = omega/D_ii (RHS_i + sum_j fac_ij p^k_j)
+//            + (1 - omega) p^k_i  for the cases still iterating, with the
+//     per-tile FP64 sums of |p^{k+1}-p^k| and |p^{k+1}|;
+//   barrier.
+// p^k lives in buffer k&1.  A case's flag for sweep k lives in act[k&1].
+// Data written by other blocks inside this launch (pressures, flags, partial
+// sums) is read with ld.global.cg so that no stale L1 line is ever used.
+// ---------------------------------------------------------------------------
+template <bool MX>
+__global__ void __launch_bounds__(256) k_sweeps(State S) {
+  using R = typename std::conditional<MX, float, double>::type;
+  __shared__ double sh[64];
+  __shared__ int any;
+  const unsigned nb = gridDim.x;
+  const int T = blockDim.x;
+  const int nc = S.ncases;
+  const R om1 = R(1.0 - S.omega);
+  const R *coef = static_cast<const R *>(S.coef);
+  const R *prhs = static_cast<const R *>(S.prhs);
+  const R *pwd = static_cast<const R *>(S.pwd);
+  const R *wc = static_cast<const R *>(S.wcoef);
+  const R *wsinv = static_cast<const R *>(S.wsinv);
+  const R *wh = static_cast<const R *>(S.wh);
+  const long long n = S.n, nwl = S.nw;
+  bool skip = S.debug_skip_barrier && blockIdx.x == 1;
+  int k = 0;
+  bool alive = true;
+  for (;;) {
+    const int cur = k & 1;
+    R *pc = static_cast<R *>(S.pb[cur]);
+    int *act_now = S.act + cur * nc;
+    const int *act_prev = S.act + (cur ^ 1) * nc;
+    // ---- decisions ----
+    for (int c = blockIdx.x; c < nc; c += nb) {
+      const CaseDev &P = S.cases[c];
+      if (k == 0) {
+        double lm = 0.0;
+        for (int q = threadIdx.x; q < P.nftile; q += T) lm = fmax(lm, __ldcg(S.tile_lam + P.ftile + q));
+        // max-reduce through the shared scratch
+        for (int o = 16; o > 0; o >>= 1) lm = fmax(lm, __shfl_xor_sync(0xffffffffu, lm, o));
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = lm;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double m = sh[0];
+          for (int w = 1; w < (T >> 5); ++w) m = fmax(m, sh[w]);
+          S.lam[c] = m;
+          act_now[c] = P.nf > 0 ? 1 : 0;
+          S.iters[c] = 0;
+          S.pstat[c] = 0;
+          S.par[c] = 0;
+          S.resid[c] = 0.0;
+        }
+        continue;
+      }
+      if (!__ldcg(act_prev + c)) {
+        if (threadIdx.x == 0) act_now[c] = 0;
+        continue;
+      }
+      double num = 0.0, den = 0.0;
+      for (int q = threadIdx.x; q < P.nftile; q += T) {
+        num += __ldcg(S.tile_part + 2 * (P.ftile + q));
+        den += __ldcg(S.tile_part + 2 * (P.ftile + q) + 1);
+      }
+      block_sum2(num, den, sh);
+      if (threadIdx.x == 0) {
+        double lam = S.residual_form == 1 ? double(P.nf) * S.lam[c] : S.lam[c];
+        double dd = lam > den ? lam : den;
+        double res = dd > 0.0 ? num / dd : num;
+        int go = 1, st = 0;
+        if (!isfinite(res)) { go = 0; st = SISPH_ENONFINITE; }
+        else if (k >= S.min_iter && res < P.tol) go = 0;
+        else if (k >= P.max_iter) { go = 0; st = SISPH_ENOTCONVERGED; }
+        S.iters[c] = k;
+        S.resid[c] = res;
+        act_now[c] = go;
+        if (!go) {
+          S.pstat[c] = st;
+          S.par[c] = cur;
+          if (st == SISPH_ENONFINITE) atomicOr(S.err, kErrNonFinite);
+          if (st == SISPH_ENOTCONVERGED) atomicOr(S.err, kErrNotConv);
+        }
+      }
+    }
+    // ---- wall extrapolation from p^k ----
+    for (int r = blockIdx.x * T + threadIdx.x; r < S.nw; r += nb * T) {
+      int w = S.wall_at[r];
+      int c = S.case_of[w];
+      if (k > 0 && !__ldcg(act_prev + c)) continue;
+      R acc = wh[r];
+      int cnt = S.wcnt[r];
+      for (int q = 0; q < cnt; ++q) {
+        long long o = (long long)q * nwl + r;
+        acc += wc[o] * __ldcg(pc + S.widx[o]);
+      }
+      R pw = acc * wsinv[r];
+      if (S.cases[c].free_surface && pw < R(0)) pw = R(0);
+      pc[w] = pw;
+    }
+    alive = grid_sync(S.bar, nb, S.barrier_budget, skip);
+    skip = false;
+    if (!alive) break;
+    if (threadIdx.x == 0) {
+      int a = 0;
+      for (int c = 0; c < nc; ++c) a |= __ldcg(act_now + c);
+      any = a;
+    }
+    __syncthreads();
+    if (!any) break;
+    // ---- damped-Jacobi sweep ----
+    R *pn = static_cast<R *>(S.pb[cur ^ 1]);
+    for (int tt = blockIdx.x; tt < S.nft; tt += nb) {
+      const Tile &t = S.ftiles[tt];
+      if (!__ldcg(act_now + t.c)) continue;
+      int i = t.beg + threadIdx.x;
+      double dn = 0.0, dp = 0.0;
+      if (i < t.end) {
+        R acc = prhs[i];
+        int cnt = S.ncnt[i];
+        for (int q = 0; q < cnt; ++q) {
+          long long o = (long long)q * n + i;
+          unsigned e = S.nbr[o];
+          acc += coef[o] * __ldcg(pc + (e & kIdxMask));
+        }
+        R po = __ldcg(pc + i);
+        R pnew = pwd[i] * acc + om1 * po;
+        pn[i] = pnew;
+        dn = fabs(double(pnew - po));
+        dp = fabs(double(pnew));
+      }
+      block_sum2(dn, dp, sh);
+      if (threadIdx.x == 0) {
+        S.tile_part[2 * tt] = dn;
+        S.tile_part[2 * tt + 1] = dp;
+      }
+    }
+    alive = grid_sync(S.bar, nb, S.barrier_budget, false);
+    if (!alive) break;
+    ++k;
+  }
+  if (!alive) return;
+  // ---- publish the final pressure of every case ----
+  for (int i = blockIdx.x * T + threadIdx.x; i < S.n; i += nb * T) {
+    int c = S.case_of[i];
+    R v = __ldcg(static_cast<const R *>(S.pb[__ldcg(S.par + c)]) + i);
+    S.p[i] = double(v);
+    if constexpr (MX) S.pf[i] = v;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int c = 0; c < nc; ++c) {
+      S.iters_tot[c] += S.iters[c];
+      S.solves[c] += 1;
+    }
+  }
+}
+
+cudaError_t launch_ppe_setup(const State &S, const Launch &L) {
+  if (L.before) L.before(L.ctx, "ppe_setup");
+  if (S.nft) {
+    if (S.dim == 2) {
+      if (S.mixed) k_setup_fluid<2, true><<<S.nft, S.T, 0, L.stream>>>(S);
+      else k_setup_fluid<2, false><<<S.nft, S.T, 0, L.stream>>>(S);
+    } else {
+      if (S.mixed) k_setup_fluid<3, true><<<S.nft, S.T, 0, L.stream>>>(S);
+      else k_setup_fluid<3, false><<<S.nft, S.T, 0, L.stream>>>(S);
+    }
+  }
+  if (S.nwt) {
+    if (S.dim == 2) {
+      if (S.mixed) k_setup_wall<2, true><<<S.nwt, S.T, 0, L.stream>>>(S);
+      else k_setup_wall<2, false><<<S.nwt, S.T, 0, L.stream>>>(S);
+    } else {
+      if (S.mixed) k_setup_wall<3, true><<<S.nwt, S.T, 0, L.stream>>>(S);
+      else k_setup_wall<3, false><<<S.nwt, S.T, 0, L.stream>>>(S);
+    }
+  }
+  if (L.after) L.after(L.ctx, "ppe_setup", double(S.n), (S.nft ? 1 : 0) + (S.nwt ? 1 : 0));
+  return cudaGetLastError();
+}
+
+int ppe_max_blocks_per_sm(const State &S, int block) {
+  int nb = 0;
+  if (S.mixed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweeps<true>, block, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweeps<false>, block, 0);
+  return nb;
+}
+
+cudaError_t launch_ppe_sweeps(const State &S, const Launch &L, int grid) {
+  cudaMemsetAsync(S.bar, 0, sizeof(Barrier), L.stream);
+  if (L.before) L.before(L.ctx, "ppe_sweeps");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(S.T);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = L.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e;
+  if (S.mixed) e = cudaLaunchKernelEx(&cfg, k_sweeps<true>, S);
+  else e = cudaLaunchKernelEx(&cfg, k_sweeps<false>, S);
+  if (L.after) L.after(L.ctx, "ppe_sweeps", 0.0, 1);
+  return e;
+}
+
+}  // namespace sisph

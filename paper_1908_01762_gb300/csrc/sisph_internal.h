@@ -1,0 +1,251 @@
+// Internal types and device helpers of libsisph (not part of the C-ABI).
+//
+// Layout.  Particles live on the device in one sorted order: case after case,
+// and inside a case its fluid block followed by its wall block:
+//   [case0 fluid | case0 wall | case1 fluid | case1 wall | ...]
+// Inside each block particles are sorted by (Morton cell, original index), so
+// the block boundaries never move and the order is deterministic.  Work is cut
+// into tiles of `T` consecutive particles that never straddle a block, so one
+// thread block handles one tile and every tile has a single case and kind.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "../../include/sisph.h"
+
+namespace sisph {
+
+constexpr int kCodeShift = 27;                   // neighbour entry = j | code << 27
+constexpr unsigned kIdxMask = (1u << kCodeShift) - 1u;
+constexpr int kMaxParticles = (1 << kCodeShift) - 1;
+
+// Error bits of the device status word.
+constexpr int kErrCapacity = 1;   // a neighbour row overflowed its capacity
+constexpr int kErrTimeout = 2;    // a grid-barrier wait ran out of budget
+constexpr int kErrNonFinite = 4;  // a PPE residual was NaN / Inf
+constexpr int kErrNotConv = 8;    // a PPE solve stopped at max_iter
+
+struct CaseDev {
+  // cell grid
+  double lo[3], hi[3], L[3], half[3];
+  double lc[3];
+  float lcf[3];
+  int nc[3];
+  int per[3];
+  int morton;              // 1: Morton-interleaved cell keys, 0: row-major
+  int bits;
+  long long slots;         // keys per (case, kind) block
+  long long key_base;      // first key of this case
+  // physics (Sec. 2-3)
+  double h, dt, rho0, nu, g[3], alpha, c0, tol, hfac;
+  int max_iter, pgrad_symm, free_surface, ustar_slip, pref_mode, K;
+  double p_ref0;
+  // derived constants
+  double cut2;             // (3h)^2, evaluated as (3*h)*(3*h)
+  double eh2;              // eta h^2
+  double inv_h, sig_h;     // quintic at h
+  double h2, inv_h2, sig_h2;  // quintic at h/2 (no-slip ghost velocity, Eq. vf)
+  double hg, inv_hg, sig_hg;  // quintic at h~ = hfac h (GTVF)
+  // layout in the sorted order
+  int fbeg, nf, wbeg, nw;
+  int wrow;                // first row of this case in the wall tables
+  int ftile, nftile;       // first fluid tile, count
+};
+
+struct Tile {
+  int beg, end, c, kind;
+};
+
+struct Barrier {
+  unsigned count;
+  unsigned gen;
+  int err;
+  int pad;
+};
+
+// Everything a kernel may need, passed by value.  Pointers are device pointers.
+struct State {
+  int dim, ncases, mixed, T;
+  int n, nf, nw, cap, wcap;
+  int nft, nwt;
+  const CaseDev *cases;
+  const Tile *ftiles, *wtiles;
+  const int *case_of;      // sorted index -> case
+  const int *wall_at;      // wall row -> sorted index
+  double omega, fs_ratio, eta;
+  int min_iter, residual_form;
+  // sort scratch
+  unsigned *key, *slot, *hist;
+  int *perm;
+  long long K;
+  // FP64 state (current buffers) and gather targets
+  double *x[3], *xn[3], *u[3], *ut[3], *m, *rho, *p;
+  int *uid;
+  double *bx[3], *bxn[3], *bu[3], *but[3], *bm, *brho, *bp;
+  int *buid;
+  double *xs[3], *us[3];   // stage-1 outputs r*, u*
+  double *uw[3], *nrm[3];  // walls: prescribed velocity, unit normal
+  double *nstar[3];        // scratch for the raw normals
+  // FP32 mirrors (MIXED)
+  float4 *pf4;             // cell-relative position, mass
+  float4 *vf4;             // velocity, density
+  float4 *utf4;            // transport velocity
+  float *pf;               // pressure
+  // neighbour lists (ELL, column-major: entry k of row i at k*n + i)
+  unsigned *nbr;
+  int *ncnt;
+  // PPE
+  void *coef;              // fac_ij per ELL slot (double or float)
+  void *prhs;              // RHS_i (active) else 0
+  void *pwd;               // omega / D_ii (active) else 0
+  void *pb[2];             // pressure ping-pong buffers
+  double *rhs_out, *diag_out;
+  int *wcnt;               // wall Shepard rows (fluid neighbours only)
+  int *widx;
+  void *wcoef;             // W_wf per entry
+  void *wsinv, *wh;        // 1/sum W, (g . sum rho r W)
+  double *tile_part;       // per fluid tile: sum|dp|, sum|p|
+  double *tile_lam;        // per fluid tile: max |RHS/D|
+  int *act;                // [2][ncases] case still iterating
+  int *iters, *pstat, *par;// per case: sweeps, status, final buffer parity
+  double *resid, *lam;
+  long long *iters_tot, *solves;
+  double *pref;            // per case background pressure in use
+  int *pref_set;
+  Barrier *bar;
+  int *err;
+  // GTVF
+  double *dg[2][3];        // FP64 displacement ping-pong
+  float4 *dgf[2];          // FP32 displacement ping-pong
+  double *vgt[3];          // sub-step velocity
+  // debug
+  long long barrier_budget;
+  int debug_skip_barrier;
+};
+
+// ---------------------------------------------------------------------------
+// Quintic spline with support 3h (reading of "the quintic spline", Sec. 2.1):
+//   W = sigma [ (3-q)^5 - 6 (2-q)^5 + 15 (1-q)^5 ], each term where positive;
+//   sigma = 7/(478 pi h^2) in 2D, 1/(120 pi h^3) in 3D.
+// poly_w / poly_dw return the bracket and its derivative in q.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R poly_w(R q) {
+  R w = R(0);
+  if (q < R(3)) { R t = R(3) - q, t2 = t * t; w = t2 * t2 * t; }
+  if (q < R(2)) { R t = R(2) - q, t2 = t * t; w -= R(6) * t2 * t2 * t; }
+  if (q < R(1)) { R t = R(1) - q, t2 = t * t; w += R(15) * t2 * t2 * t; }
+  return w;
+}
+
+template <typename R>
+__device__ __forceinline__ R poly_dw(R q) {
+  R d = R(0);
+  if (q < R(3)) { R t = R(3) - q, t2 = t * t; d = R(-5) * t2 * t2; }
+  if (q < R(2)) { R t = R(2) - q, t2 = t * t; d += R(30) * t2 * t2; }
+  if (q < R(1)) { R t = R(1) - q, t2 = t * t; d -= R(75) * t2 * t2; }
+  return d;
+}
+
+__host__ __device__ inline double quintic_sigma(double h, int dim) {
+  const double pi = 3.14159265358979323846;
+  return dim == 2 ? 7.0 / (478.0 * pi * h * h) : 1.0 / (120.0 * pi * h * h * h);
+}
+
+// q = r / h.  The FP64 form divides, exactly as the definition reads, so that
+// a pair within rounding of the support edge gets the same (zero or tiny)
+// weight as in a plain evaluation; the FP32 form multiplies by 1/h.
+template <typename R>
+__device__ __forceinline__ R qof(R r, double h, double inv_h) {
+  if constexpr (std::is_same<R, float>::value) return r * float(inv_h);
+  else return r / h;
+}
+
+template <typename R>
+__device__ __forceinline__ R sqrt_r(R v) {
+  if constexpr (std::is_same<R, float>::value) return sqrtf(v);
+  else return sqrt(v);
+}
+
+// Minimum-image pair vector r_ij = r_i - r_j from FP64 positions, and
+// |r_ij|^2 = dx*dx + dy*dy (+ dz*dz) evaluated left to right, unfused.
+template <int DIM>
+__device__ __forceinline__ double pair_d(const CaseDev &P, const double xi[3],
+                                         double *const x[3], int j, double d[3]) {
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    double t = xi[k] - x[k][j];
+    if (P.per[k]) {
+      if (t > P.half[k]) t -= P.L[k];
+      else if (t < -P.half[k]) t += P.L[k];
+    }
+    d[k] = t;
+  }
+  double r2 = __dmul_rn(d[0], d[0]);
+  r2 = __dadd_rn(r2, __dmul_rn(d[1], d[1]));
+  if (DIM == 3) r2 = __dadd_rn(r2, __dmul_rn(d[2], d[2]));
+  return r2;
+}
+
+// Pair vector from FP32 cell-relative positions: r_ij = rel_i - rel_j - o lc,
+// where o is the stencil offset (code) of j's cell seen from i's cell.
+template <int DIM>
+__device__ __forceinline__ float pair_f(const CaseDev &P, const float4 &pi, const float4 &pj,
+                                        unsigned code, float d[3]) {
+  int ox = int(code % 3u) - 1;
+  int oy = int((code / 3u) % 3u) - 1;
+  d[0] = (pi.x - pj.x) - float(ox) * P.lcf[0];
+  d[1] = (pi.y - pj.y) - float(oy) * P.lcf[1];
+  float r2 = d[0] * d[0] + d[1] * d[1];
+  if (DIM == 3) {
+    int oz = int(code / 9u) - 1;
+    d[2] = (pi.z - pj.z) - float(oz) * P.lcf[2];
+    r2 += d[2] * d[2];
+  } else {
+    d[2] = 0.f;
+  }
+  return r2;
+}
+
+__device__ __forceinline__ void store_r(void *base, long long i, double v, int mixed) {
+  if (mixed) static_cast<float *>(base)[i] = float(v);
+  else static_cast<double *>(base)[i] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (one translation unit each).
+// ---------------------------------------------------------------------------
+struct Launch {
+  cudaStream_t stream;
+  void (*before)(void *ctx, const char *name);
+  void (*after)(void *ctx, const char *name, double units, int nkernels);
+  void *ctx;
+};
+
+// nbr.cu
+cudaError_t launch_sort(const State &S, const Launch &L, const double *const pos[3], int gather_mode,
+                        bool gather_static);
+cudaError_t launch_build(const State &S, const Launch &L);
+cudaError_t launch_copy_static(const State &S, const Launch &L);
+// passes.cu
+cudaError_t launch_density(const State &S, const Launch &L);
+cudaError_t launch_normals(const State &S, const Launch &L);
+cudaError_t launch_ghost(const State &S, const Launch &L, int slip_stage);
+cudaError_t launch_stage1(const State &S, const Launch &L);
+cudaError_t launch_pgrad(const State &S, const Launch &L);
+cudaError_t launch_pref(const State &S, const Launch &L);
+cudaError_t launch_gtvf(const State &S, const Launch &L, int kmax);
+cudaError_t launch_update(const State &S, const Launch &L);
+cudaError_t launch_scatter_field(const State &S, const Launch &L, const void *src, int is_float,
+                                 int stride_f4, int comp, double *dst_user);
+cudaError_t launch_gather_field(const State &S, const Launch &L, const double *src_user, double *dst);
+cudaError_t launch_scatter_disp(const State &S, const Launch &L, int comp, double *dst_user);
+cudaError_t launch_refresh_mirrors(const State &S, const Launch &L);
+// ppe.cu
+cudaError_t launch_ppe_setup(const State &S, const Launch &L);
+cudaError_t launch_ppe_sweeps(const State &S, const Launch &L, int grid);
+int ppe_max_blocks_per_sm(const State &S, int block);
+
+}  // namespace sisph

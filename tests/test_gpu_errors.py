@@ -1,0 +1,74 @@
+"""Failure detection without a GPU fault: every device-side failure comes back
+as a status code from a bounded wait or a status word, and the process and
+device stay usable.  Failures are made on the host (bad inputs, a tolerance
+that cannot be met, a capacity that is too small) or by a wait that runs out
+(a test hook that keeps one block from arriving at the first grid barrier,
+with a 5 ms budget)."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sisph():
+    import paper_1908_01762_gb300 as pkg
+    pkg.build()
+    from paper_1908_01762_gb300 import sisph as mod
+    mod.load_library()
+    return mod
+
+
+def test_not_converged_is_reported_and_state_valid(sisph):
+    case = dict(workloads.taylor_green(30))
+    case["params"] = dict(case["params"], tol=1e-14, max_iter=1)
+    sim = sisph.Simulation(case)
+    rc = sim.step(2)
+    assert rc == sisph.ENOTCONVERGED
+    st = sim.stats()[0]
+    assert st.status == sisph.ENOTCONVERGED and st.iters == 1
+    assert np.all(np.isfinite(sim.get("p")))
+    sim.close()
+
+
+def test_non_finite_input_is_reported(sisph):
+    case = workloads.taylor_green(30)
+    case = dict(case, u=case["u"].copy())
+    case["u"][17] = np.nan
+    sim = sisph.Simulation(case)
+    with pytest.raises(sisph.SisphError) as ei:
+        sim.step(1)
+    assert ei.value.code == sisph.ENONFINITE
+    sim.close()
+
+
+def test_barrier_timeout_returns_status_and_device_recovers(sisph):
+    case = workloads.taylor_green(40)
+    sim = sisph.Simulation(case, debug_skip_barrier=1, barrier_timeout_ms=5.0)
+    sim.density()
+    with pytest.raises(sisph.SisphError) as ei:
+        sim.ppe_solve(1e-4, 50)
+    assert ei.value.code == sisph.ETIMEOUT
+    sim.close()
+    ok = sisph.Simulation(case)
+    ok.density()
+    rc, it, res = ok.ppe_solve(1e-2, 50)
+    assert it[0] >= 2
+    ok.close()
+
+
+def test_neighbor_capacity_overflow_is_reported(sisph):
+    with pytest.raises(sisph.SisphError) as ei:
+        sisph.Simulation(workloads.taylor_green(30), nbr_capacity=8)
+    assert ei.value.code == sisph.ECAPACITY
+
+
+def test_invalid_field_and_stream(sisph):
+    sim = sisph.Simulation(workloads.taylor_green(20))
+    with pytest.raises(sisph.SisphError):
+        sim.set("nx", np.zeros(sim.n))
+    with pytest.raises(sisph.SisphError):
+        sim.set("z", np.zeros(sim.n))
+    sim.close()
