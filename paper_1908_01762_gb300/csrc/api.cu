@@ -555,8 +555,9 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   }
   A(&S.m, N); A(&S.rho, N); A(&S.p, N); A(&S.uid, N);
   A(&S.bm, N); A(&S.brho, N); A(&S.bp, N); A(&S.buid, N);
+  A(&S.pf4, N);
   if (S.mixed) {
-    A(&S.pf4, N); A(&S.vf4, N); A(&S.utf4, N); A(&S.pf, N);
+    A(&S.vf4, N); A(&S.utf4, N); A(&S.pf, N);
     A(&S.dgf[0], N); A(&S.dgf[1], N);
   }
   A(&S.nbr, N * size_t(S.cap));
@@ -584,7 +585,7 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   A(&S.tile_part, 2 * size_t(std::max(1, S.nft)));
   A(&S.tile_lam, size_t(std::max(1, S.nft)));
   A(&S.act, 2 * size_t(ncases));
-  A(&S.iters, ncases); A(&S.pstat, ncases); A(&S.par, ncases);
+  A(&S.iters, ncases); A(&S.pstat, ncases); A(&S.par, 2 * size_t(ncases));
   A(&S.resid, ncases); A(&S.lam, ncases);
   A(&S.iters_tot, ncases); A(&S.solves, ncases);
   A(&S.pref, ncases); A(&S.pref_set, ncases);

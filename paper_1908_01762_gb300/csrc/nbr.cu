@@ -219,6 +219,16 @@ __global__ void k_gather(State S, int mode, int gather_static) {
     S.utf4[dst] = make_float4(float(tt[0]), float(tt[1]), float(tt[2]), 0.f);
     S.pf[dst] = float(S.p[src]);
   }
+  // FP32 position relative to the particle's own cell, and its mass: the
+  // neighbour build pre-tests pairs on it, the MIXED sums use it throughout
+  const CaseDev &P = S.cases[S.case_of[dst]];
+  double xi[3] = {0.0, 0.0, 0.0};
+  _Pragma("unroll") for (int k = 0; k < DIM; ++k) xi[k] = S.bx[k][dst];
+  int c[3];
+  cell_of<DIM>(P, xi, c);
+  float rel[3] = {0.f, 0.f, 0.f};
+  _Pragma("unroll") for (int k = 0; k < DIM; ++k) rel[k] = float(xi[k] - (P.lo[k] + double(c[k]) * P.lc[k]));
+  S.pf4[dst] = make_float4(rel[0], rel[1], rel[2], float(S.m[src]));
 }
 
 __global__ void k_copy_static(State S) {
@@ -229,9 +239,14 @@ __global__ void k_copy_static(State S) {
 }
 
 // One thread per particle: scan the 3^d stencil of cells (fluid block, then
-// wall block of each cell), test the FP64 predicate, append to the ELL row.
+// wall block of each cell) and append every j with |r_ij|^2 < (3h)^2 to the
+// ELL row.  Each candidate is first tested in FP32 on cell-relative
+// coordinates; only pairs within a relative band of 1e-4 around the cutoff
+// (the FP32 error is below 1e-5 of (3h)^2 for positions inside their cell)
+// go to the exact unfused FP64 test, so the set equals the FP64 definition.
+// Particles clamped far outside a non-periodic box take the FP64 test always.
 template <int DIM>
-__global__ void k_build(State S) {
+__global__ void __launch_bounds__(256) k_build(State S) {
   const Tile &t = tile_of(S, blockIdx.x);
   int i = t.beg + threadIdx.x;
   if (i >= t.end) return;
@@ -239,12 +254,12 @@ __global__ void k_build(State S) {
   double xi[3] = {S.x[0][i], S.x[1][i], DIM == 3 ? S.x[2][i] : 0.0};
   int c[3];
   cell_of<DIM>(P, xi, c);
-  if (S.mixed) {
-    float rel[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) rel[k] = float(xi[k] - (P.lo[k] + double(c[k]) * P.lc[k]));
-    S.pf4[i] = make_float4(rel[0], rel[1], rel[2], float(S.m[i]));
-  }
+  const float4 pi = S.pf4[i];
+  const float lx = P.lcf[0], ly = P.lcf[1], lz = P.lcf[2];
+  const float lim = 1.5f * fmaxf(lx, fmaxf(ly, DIM == 3 ? lz : ly));
+  const bool out_i = fabsf(pi.x) > lim || fabsf(pi.y) > lim || (DIM == 3 && fabsf(pi.z) > lim);
+  const float cut2f = float(P.cut2);
+  const float lo_band = cut2f * (1.0f - 1e-4f), hi_band = cut2f * (1.0f + 1e-4f);
   const int zr = (DIM == 3) ? 1 : 0;
   int cnt = 0;
   bool over = false;
@@ -255,8 +270,7 @@ __global__ void k_build(State S) {
         int o[3] = {ox, oy, oz};
         int cn[3] = {c[0], c[1], c[2]};
         bool skip = false;
-#pragma unroll
-        for (int k = 0; k < DIM; ++k) {
+        _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
           int v = c[k] + o[k];
           if (v < 0 || v >= P.nc[k]) {
             if (P.per[k]) v = (v + P.nc[k]) % P.nc[k];
@@ -265,16 +279,30 @@ __global__ void k_build(State S) {
           cn[k] = v;
         }
         if (skip) continue;
-        unsigned code = unsigned((ox + 1) + 3 * (oy + 1) + 9 * (oz + 1));
+        const unsigned code = unsigned((ox + 1) + 3 * (oy + 1) + 9 * (oz + 1));
+        const float fx = pi.x - float(ox) * lx, fy = pi.y - float(oy) * ly, fz = pi.z - float(oz) * lz;
         long long m = cell_key<DIM>(P, cn);
         for (int kind = 0; kind < 2; ++kind) {
           if (kind == 1 && P.nw == 0) break;
           long long q = P.key_base + (long long)kind * P.slots + m;
           unsigned beg = S.hist[q], end = S.hist[q + 1];
           for (unsigned j = beg; j < end; ++j) {
-            double d[3];
-            double r2 = pair_d<DIM>(P, xi, S.x, int(j), d);
-            if (r2 < P.cut2) {
+            float4 pj = S.pf4[j];
+            float dx = fx - pj.x, dy = fy - pj.y;
+            float r2f = dx * dx + dy * dy;
+            if (DIM == 3) {
+              float dz = fz - pj.z;
+              r2f += dz * dz;
+            }
+            bool in;
+            bool out_j = fabsf(pj.x) > lim || fabsf(pj.y) > lim || (DIM == 3 && fabsf(pj.z) > lim);
+            if (!out_i && !out_j && r2f < lo_band) in = true;
+            else if (!out_i && !out_j && r2f > hi_band) in = false;
+            else {
+              double d[3];
+              in = pair_d<DIM>(P, xi, S.x, int(j), d) < P.cut2;
+            }
+            if (in) {
               if (cnt < S.cap) S.nbr[(long long)cnt * nn + i] = j | (code << kCodeShift);
               else over = true;
               ++cnt;

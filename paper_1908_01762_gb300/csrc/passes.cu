@@ -69,6 +69,7 @@ __device__ __forceinline__ void tvel(const State &S, int j, R u[3]) {
   {                                                            \
     const int _cnt = S.ncnt[i];                                \
     const long long _n = S.n;                                  \
+    _Pragma("unroll 4")                                        \
     for (int _k = 0; _k < _cnt; ++_k) {                        \
       const unsigned e = S.nbr[(long long)_k * _n + i];        \
       __VA_ARGS__                                              \

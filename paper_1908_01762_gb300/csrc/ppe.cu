@@ -235,27 +235,29 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double *sh) {
 }
 
 // ---------------------------------------------------------------------------
-// Persistent damped-Jacobi solve for all cases.  Iteration k:
-//   W phase: each case's owner block decides from the partial sums of
-//     sweep k-1 whether the case goes on (Eq. convergence; at least
-//     min_iter sweeps, at most max_iter); every case that swept last time
-//     extrapolates its wall pressure from p^k (Eq. p-shepard, clamped at 0
-//     for free-surface flows) -- for a finished case this is the final
-//     wall update;
-//   barrier;
-//   F phase: p^{k+1}_i = omega/D_ii (RHS_i + sum_j fac_ij p^k_j)
-//            + (1 - omega) p^k_i  for the cases still iterating, with the
-//     per-tile FP64 sums of |p^{k+1}-p^k| and |p^{k+1}|;
-//   barrier.
-// p^k lives in buffer k&1.  A case's flag for sweep k lives in act[k&1].
-// Data written by other blocks inside this launch (pressures, flags, partial
-// sums) is read with ld.global.cg so that no stale L1 line is ever used.
+// Persistent damped-Jacobi solve for all cases, one launch.
+//   W phase k: every case that swept in F phase k-1 (or k = 0) extrapolates
+//     its wall pressure from p^k (Eq. p-shepard, clamped at 0 for
+//     free-surface flows); for a case that has just finished this is the
+//     final wall update.  Skipped, with its barrier, when no case has walls.
+//   F phase k: for every unfinished case
+//       p^{k+1}_i = omega/D_ii (RHS_i + sum_j fac_ij p^k_j) + (1 - omega) p^k_i
+//     with per-tile FP64 sums of |p^{k+1}-p^k| and |p^{k+1}|.  The block that
+//     completes the last tile of a case (per-case arrival counter) adds that
+//     case's tile sums in tile order -- the same order whoever arrives last --
+//     and applies Eq. convergence: at least min_iter sweeps, at most max_iter.
+//   grid barrier after each phase.
+// p^k lives in buffer k&1.  Pressures written by other blocks are read with
+// ordinary (L1-cached) loads: every grid barrier ends with an acquire fence
+// in the block's master thread followed by a block barrier, which orders
+// those reads after the other blocks' writes.  Flags and partial sums are
+// read with ld.global.cg.
 // ---------------------------------------------------------------------------
 template <bool MX>
 __global__ void __launch_bounds__(256) k_sweeps(State S) {
   using R = typename std::conditional<MX, float, double>::type;
   __shared__ double sh[64];
-  __shared__ int any;
+  __shared__ int flag;
   const unsigned nb = gridDim.x;
   const int T = blockDim.x;
   const int nc = S.ncases;
@@ -267,107 +269,62 @@ __global__ void __launch_bounds__(256) k_sweeps(State S) {
   const R *wsinv = static_cast<const R *>(S.wsinv);
   const R *wh = static_cast<const R *>(S.wh);
   const long long n = S.n, nwl = S.nw;
+  int *done = S.act;                 // [nc] case finished
+  int *fin = S.act + nc;             // [nc] sweep count at which it finished
+  unsigned *arrive = reinterpret_cast<unsigned *>(S.par + nc);  // [nc]
   bool skip = S.debug_skip_barrier && blockIdx.x == 1;
-  int k = 0;
   bool alive = true;
+  // hard bound on the loop: every case stops at its max_iter at the latest
+  int kcap = 0;
+  for (int c = 0; c < nc; ++c) kcap = max(kcap, S.cases[c].max_iter);
+  int k = 0;
   for (;;) {
     const int cur = k & 1;
     R *pc = static_cast<R *>(S.pb[cur]);
-    int *act_now = S.act + cur * nc;
-    const int *act_prev = S.act + (cur ^ 1) * nc;
-    // ---- decisions ----
-    for (int c = blockIdx.x; c < nc; c += nb) {
-      const CaseDev &P = S.cases[c];
-      if (k == 0) {
-        double lm = 0.0;
-        for (int q = threadIdx.x; q < P.nftile; q += T) lm = fmax(lm, __ldcg(S.tile_lam + P.ftile + q));
-        // max-reduce through the shared scratch
-        for (int o = 16; o > 0; o >>= 1) lm = fmax(lm, __shfl_xor_sync(0xffffffffu, lm, o));
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = lm;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          double m = sh[0];
-          for (int w = 1; w < (T >> 5); ++w) m = fmax(m, sh[w]);
-          S.lam[c] = m;
-          act_now[c] = P.nf > 0 ? 1 : 0;
-          S.iters[c] = 0;
-          S.pstat[c] = 0;
-          S.par[c] = 0;
-          S.resid[c] = 0.0;
+    // ---- W phase: wall extrapolation from p^k ----
+    if (S.nw > 0) {
+      for (int r = blockIdx.x * T + threadIdx.x; r < S.nw; r += nb * T) {
+        int w = S.wall_at[r];
+        int c = S.case_of[w];
+        if (k > 0 && __ldcg(done + c) && __ldcg(fin + c) != k) continue;
+        R acc = wh[r];
+        int cnt = S.wcnt[r];
+        for (int q = 0; q < cnt; ++q) {
+          long long o = (long long)q * nwl + r;
+          acc += wc[o] * pc[S.widx[o]];
         }
-        continue;
+        R pw = acc * wsinv[r];
+        if (S.cases[c].free_surface && pw < R(0)) pw = R(0);
+        pc[w] = pw;
       }
-      if (!__ldcg(act_prev + c)) {
-        if (threadIdx.x == 0) act_now[c] = 0;
-        continue;
-      }
-      double num = 0.0, den = 0.0;
-      for (int q = threadIdx.x; q < P.nftile; q += T) {
-        num += __ldcg(S.tile_part + 2 * (P.ftile + q));
-        den += __ldcg(S.tile_part + 2 * (P.ftile + q) + 1);
-      }
-      block_sum2(num, den, sh);
-      if (threadIdx.x == 0) {
-        double lam = S.residual_form == 1 ? double(P.nf) * S.lam[c] : S.lam[c];
-        double dd = lam > den ? lam : den;
-        double res = dd > 0.0 ? num / dd : num;
-        int go = 1, st = 0;
-        if (!isfinite(res)) { go = 0; st = SISPH_ENONFINITE; }
-        else if (k >= S.min_iter && res < P.tol) go = 0;
-        else if (k >= P.max_iter) { go = 0; st = SISPH_ENOTCONVERGED; }
-        S.iters[c] = k;
-        S.resid[c] = res;
-        act_now[c] = go;
-        if (!go) {
-          S.pstat[c] = st;
-          S.par[c] = cur;
-          if (st == SISPH_ENONFINITE) atomicOr(S.err, kErrNonFinite);
-          if (st == SISPH_ENOTCONVERGED) atomicOr(S.err, kErrNotConv);
-        }
-      }
+      alive = grid_sync(S.bar, nb, S.barrier_budget, skip);
+      skip = false;
+      if (!alive) break;
     }
-    // ---- wall extrapolation from p^k ----
-    for (int r = blockIdx.x * T + threadIdx.x; r < S.nw; r += nb * T) {
-      int w = S.wall_at[r];
-      int c = S.case_of[w];
-      if (k > 0 && !__ldcg(act_prev + c)) continue;
-      R acc = wh[r];
-      int cnt = S.wcnt[r];
-      for (int q = 0; q < cnt; ++q) {
-        long long o = (long long)q * nwl + r;
-        acc += wc[o] * __ldcg(pc + S.widx[o]);
-      }
-      R pw = acc * wsinv[r];
-      if (S.cases[c].free_surface && pw < R(0)) pw = R(0);
-      pc[w] = pw;
+    // ---- any case left?  (a case without fluid has nothing to solve) ----
+    int mine = 0;
+    for (int c = threadIdx.x; c < nc; c += T) mine |= (__ldcg(done + c) == 0 && S.cases[c].nf > 0);
+    if (!__syncthreads_or(mine)) break;
+    if (k >= kcap) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(S.err, kErrNotConv);
+      break;
     }
-    alive = grid_sync(S.bar, nb, S.barrier_budget, skip);
-    skip = false;
-    if (!alive) break;
-    if (threadIdx.x == 0) {
-      int a = 0;
-      for (int c = 0; c < nc; ++c) a |= __ldcg(act_now + c);
-      any = a;
-    }
-    __syncthreads();
-    if (!any) break;
-    // ---- damped-Jacobi sweep ----
+    // ---- F phase: one damped-Jacobi sweep of the unfinished cases ----
     R *pn = static_cast<R *>(S.pb[cur ^ 1]);
     for (int tt = blockIdx.x; tt < S.nft; tt += nb) {
       const Tile &t = S.ftiles[tt];
-      if (!__ldcg(act_now + t.c)) continue;
+      if (__ldcg(done + t.c)) continue;
       int i = t.beg + threadIdx.x;
       double dn = 0.0, dp = 0.0;
       if (i < t.end) {
         R acc = prhs[i];
         int cnt = S.ncnt[i];
-        for (int q = 0; q < cnt; ++q) {
+        _Pragma("unroll 4") for (int q = 0; q < cnt; ++q) {
           long long o = (long long)q * n + i;
           unsigned e = S.nbr[o];
-          acc += coef[o] * __ldcg(pc + (e & kIdxMask));
+          acc += coef[o] * pc[e & kIdxMask];
         }
-        R po = __ldcg(pc + i);
+        R po = pc[i];
         R pnew = pwd[i] * acc + om1 * po;
         pn[i] = pnew;
         dn = fabs(double(pnew - po));
@@ -377,9 +334,62 @@ __global__ void __launch_bounds__(256) k_sweeps(State S) {
       if (threadIdx.x == 0) {
         S.tile_part[2 * tt] = dn;
         S.tile_part[2 * tt + 1] = dp;
+        __threadfence();
+        const CaseDev &P = S.cases[t.c];
+        flag = (atomicAdd(arrive + t.c, 1u) == unsigned(P.nftile - 1));
+      }
+      __syncthreads();
+      if (flag) {
+        // last tile of this case: Eq. convergence over all of its tiles
+        __threadfence();
+        const int c = t.c;
+        const CaseDev &P = S.cases[c];
+        double num = 0.0, den = 0.0, lm = 0.0;
+        for (int q = threadIdx.x; q < P.nftile; q += T) {
+          num += __ldcg(S.tile_part + 2 * (P.ftile + q));
+          den += __ldcg(S.tile_part + 2 * (P.ftile + q) + 1);
+          if (k == 0) lm = fmax(lm, __ldcg(S.tile_lam + P.ftile + q));
+        }
+        block_sum2(num, den, sh);
+        if (k == 0) {
+          for (int o = 16; o > 0; o >>= 1) lm = fmax(lm, __shfl_xor_sync(0xffffffffu, lm, o));
+          __syncthreads();
+          if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = lm;
+          __syncthreads();
+          if (threadIdx.x == 0) {
+            double m = sh[0];
+            for (int w = 1; w < (T >> 5); ++w) m = fmax(m, sh[w]);
+            S.lam[c] = m;
+          }
+        }
+        if (threadIdx.x == 0) {
+          const int kk = k + 1;                    // sweeps completed
+          const double lamc = S.lam[c];
+          double lam = S.residual_form == 1 ? double(P.nf) * lamc : lamc;
+          double dd = lam > den ? lam : den;
+          double res = dd > 0.0 ? num / dd : num;
+          int go = 1, st = 0;
+          if (!isfinite(res)) { go = 0; st = SISPH_ENONFINITE; }
+          else if (kk >= S.min_iter && res < P.tol) go = 0;
+          else if (kk >= P.max_iter) { go = 0; st = SISPH_ENOTCONVERGED; }
+          S.iters[c] = kk;
+          S.resid[c] = res;
+          arrive[c] = 0u;
+          if (!go) {
+            S.pstat[c] = st;
+            S.par[c] = kk & 1;
+            fin[c] = kk;
+            __threadfence();
+            done[c] = 1;
+            if (st == SISPH_ENONFINITE) atomicOr(S.err, kErrNonFinite);
+            if (st == SISPH_ENOTCONVERGED) atomicOr(S.err, kErrNotConv);
+          }
+        }
+        __syncthreads();
       }
     }
-    alive = grid_sync(S.bar, nb, S.barrier_budget, false);
+    alive = grid_sync(S.bar, nb, S.barrier_budget, skip);
+    skip = false;
     if (!alive) break;
     ++k;
   }
@@ -432,6 +442,11 @@ int ppe_max_blocks_per_sm(const State &S, int block) {
 
 cudaError_t launch_ppe_sweeps(const State &S, const Launch &L, int grid) {
   cudaMemsetAsync(S.bar, 0, sizeof(Barrier), L.stream);
+  // done[nc], fin[nc] = 0; par[nc] and the arrival counters par[nc..2nc) = 0
+  cudaMemsetAsync(S.act, 0, 2 * sizeof(int) * size_t(S.ncases), L.stream);
+  cudaMemsetAsync(S.par, 0, 2 * sizeof(int) * size_t(S.ncases), L.stream);
+  cudaMemsetAsync(S.iters, 0, sizeof(int) * size_t(S.ncases), L.stream);
+  cudaMemsetAsync(S.pstat, 0, sizeof(int) * size_t(S.ncases), L.stream);
   if (L.before) L.before(L.ctx, "ppe_sweeps");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);

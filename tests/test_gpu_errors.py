@@ -72,3 +72,31 @@ def test_invalid_field_and_stream(sisph):
     with pytest.raises(sisph.SisphError):
         sim.set("z", np.zeros(sim.n))
     sim.close()
+
+
+def test_batch_with_a_walls_only_case_terminates(sisph):
+    """A case without fluid has nothing to solve; the batch still converges."""
+    tank = workloads.still_tank_2d(6, 6, dx=0.1)
+    walls = {k: (v[tank["kind"] == 1] if isinstance(v, np.ndarray) and v.shape == (tank["n"],) else v)
+             for k, v in tank.items()}
+    walls["n"] = int(np.sum(tank["kind"] == 1))
+    sim = sisph.Simulation([workloads.taylor_green(20, tol=1e-2), walls])
+    rc = sim.step(3)
+    st = sim.stats()
+    assert st[0].iters >= 2 and st[1].iters == 0
+    assert np.all(np.isfinite(sim.get("p")))
+    sim.close()
+
+
+def test_all_free_surface_case(sisph):
+    """A sparse blob: every fluid particle is below 0.8 rho0, so p stays 0."""
+    blob = workloads.still_tank_2d(3, 3, dx=0.1)
+    blob = dict(blob, x=blob["x"] * 1.0, y=blob["y"] * 1.0)
+    fl = blob["kind"] == 0
+    blob["x"] = np.where(fl, blob["x"] * 2.2, blob["x"])
+    blob["y"] = np.where(fl, blob["y"] * 2.2 + 1.0, blob["y"])   # clear of the walls
+    sim = sisph.Simulation(blob)
+    sim.step(2)
+    assert np.all(sim.get("p")[fl] == 0.0)
+    assert sim.stats()[0].iters >= 2
+    sim.close()
