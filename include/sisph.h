@@ -231,6 +231,42 @@ int sisph_load(sisph_t s, const char *path);
 const char *sisph_last_error(sisph_t s);
 const char *sisph_version(void);
 
+/* Neighbour search that allocates no memory.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- an
+ * application whose device memory is already fully reserved by its own
+ * allocator, or a latency-critical loop that must not pay for cudaMalloc and
+ * cudaFree, which can synchronise the device.
+ *
+ * Same search as sisph_build_neighbors (N(i) = {j : |r_ij|^2 < (3h)^2},
+ * minimum image in periodic directions, |r_ij|^2 = dx*dx + dy*dy (+ dz*dz)
+ * unfused, i itself included) for n points given in DEVICE memory
+ * (x_dev, y_dev, z_dev; z_dev may be NULL when dim == 2; positions must lie in
+ * [lo, hi) in periodic directions).  Output, also in DEVICE memory the caller
+ * allocated: counts_dev[n] and idx_dev[n * cap], row i at idx_dev + i * cap
+ * holding the indices of N(i) in ascending order.  Kernels run on `stream`
+ * (a cudaStream_t; NULL = the default stream) and the call waits for them.
+ *
+ * All scratch memory (cell histogram, cell ids, slots, the sort permutation,
+ * a status word; about 1 MiB) is one fixed device array reserved when the
+ * library is loaded; every GPU that loads the library holds it until the
+ * process exits.  Limits: n <= SISPH_NOALLOC_MAX_POINTS points and a cell
+ * grid (cells of side >= 3h over [lo, hi)) of at most SISPH_NOALLOC_MAX_CELLS
+ * cells; larger inputs are rejected with SISPH_EINVAL and a message.  A row
+ * with more than cap neighbours returns SISPH_ECAPACITY (its count is
+ * clipped to cap).  The first call on each device looks up the device address
+ * of the scratch array with that device current; make that first call before
+ * any stream capture begins.  Every call shares the array and it keeps the
+ * last call's contents (each call clears what must start at zero); calls
+ * whose kernels overlap on the GPU race on it, so serialise them.  The
+ * library calls no cudaMalloc, cudaFree or allocating routine here.  Errors
+ * are reported through sisph_last_error(NULL). */
+#define SISPH_NOALLOC_MAX_POINTS 65536
+#define SISPH_NOALLOC_MAX_CELLS 65536
+int sisph_neighbors_noalloc(int32_t dim, int32_t n, const double *x_dev, const double *y_dev,
+                            const double *z_dev, double h, const double lo[3], const double hi[3],
+                            const int32_t periodic[3], int32_t cap, int32_t *counts_dev,
+                            int32_t *idx_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

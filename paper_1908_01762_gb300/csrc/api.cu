@@ -20,6 +20,15 @@ namespace {
 
 thread_local std::string g_create_error;
 
+}  // namespace
+
+namespace sisph {
+// Error message of a call that has no handle (creation, the no-alloc search).
+void set_global_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace sisph
+
+namespace {
+
 struct Pending {
   std::string name;
   double units;

@@ -100,6 +100,9 @@ def load_library(path: str = LIB_PATH):
         "sisph_load": (C.c_int, [h, C.c_char_p]),
         "sisph_last_error": (C.c_char_p, [h]),
         "sisph_version": (C.c_char_p, []),
+        "sisph_neighbors_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                              C.c_void_p, C.c_double, _dp, _dp, _ip, C.c_int32,
+                                              C.c_void_p, C.c_void_p, C.c_void_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -289,6 +292,22 @@ def sisph_last_error(h=None):
 
 def sisph_version():
     return load_library().sisph_version().decode()
+
+
+def sisph_neighbors_noalloc(dim, n, x_ptr, y_ptr, z_ptr, h, lo, hi, periodic, cap,
+                            counts_ptr, idx_ptr, stream_ptr=None):
+    """Neighbour search without allocation; every pointer is a device address.
+
+    Scratch lives in a fixed device array inside the library, for callers
+    that cannot allocate device memory themselves (see include/sisph.h)."""
+    lo_a = (C.c_double * 3)(*lo)
+    hi_a = (C.c_double * 3)(*hi)
+    per_a = (C.c_int32 * 3)(*periodic)
+    rc = load_library().sisph_neighbors_noalloc(
+        int(dim), int(n), C.c_void_p(x_ptr), C.c_void_p(y_ptr), C.c_void_p(z_ptr or 0), float(h),
+        C.cast(lo_a, _dp), C.cast(hi_a, _dp), C.cast(per_a, _ip), int(cap),
+        C.c_void_p(counts_ptr), C.c_void_p(idx_ptr), C.c_void_p(stream_ptr or 0))
+    return _check(rc, None)
 
 
 class Simulation:
