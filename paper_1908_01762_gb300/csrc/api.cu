@@ -244,9 +244,17 @@ cudaError_t do_step(sisph_t s) {
   if (e == cudaSuccess) e = do_build(s, 1, false);    // neighbours at r*
   if (e == cudaSuccess) e = do_ppe(s);                // Eqs. sph-ppe, p-sor, convergence
   if (e == cudaSuccess) e = launch_pref(s->S, L);     // p_ref after the first solve
+  if (s->S.mixed) {
+    // one pass for the cases with K = 1; separate GTVF sub-steps and update
+    // only for cases with K > 1
+    if (e == cudaSuccess) e = launch_pgrad_gtvf1(s->S, L);
+    if (e == cudaSuccess && s->kmax > 1) e = launch_gtvf(s->S, L, s->kmax, 1);
+    if (e == cudaSuccess && s->kmax > 1) e = launch_update(s->S, L, 1);
+    return e;
+  }
   if (e == cudaSuccess) e = launch_pgrad(s->S, L);    // Eq. int:vnp1
-  if (e == cudaSuccess) e = launch_gtvf(s->S, L, s->kmax);  // Eqs. int:gtvf:*
-  if (e == cudaSuccess) e = launch_update(s->S, L);   // Eqs. int:vhatnp2, int:rnp2
+  if (e == cudaSuccess) e = launch_gtvf(s->S, L, s->kmax, 0);  // Eqs. int:gtvf:*
+  if (e == cudaSuccess) e = launch_update(s->S, L, 0);   // Eqs. int:vhatnp2, int:rnp2
   return e;
 }
 
@@ -301,6 +309,7 @@ int setup_case(sisph_t s, int c, const sisph_particles &P, const sisph_case_para
     if (k >= dim) {
       D.nc[k] = 1;
       D.lc[k] = 1.0;
+      D.inv_lc[k] = 1.0;
       D.lcf[k] = 1.f;
       continue;
     }
@@ -319,6 +328,7 @@ int setup_case(sisph_t s, int c, const sisph_particles &P, const sisph_case_para
       D.nc[k] = std::max(1, int(ncd));
     }
     D.lcf[k] = float(D.lc[k]);
+    D.inv_lc[k] = 1.0 / D.lc[k];
     maxnc = std::max(maxnc, D.nc[k]);
   }
   int bits = 0;
@@ -450,7 +460,7 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
     }
     ntot += P.n;
   }
-  if (ntot > kMaxParticles) return fail(nullptr, SISPH_EINVAL, "too many particles (max 2^27 - 1)");
+  if (ntot > kMaxParticles) return fail(nullptr, SISPH_EINVAL, "too many particles (max 2^26 - 1)");
 
   sisph_t s = new sisph_s();
   s->opt = opt;

@@ -29,7 +29,9 @@ __device__ __forceinline__ void cell_of(const CaseDev &P, const double xi[3], in
   c[2] = 0;
 #pragma unroll
   for (int k = 0; k < DIM; ++k) {
-    double t = floor((xi[k] - P.lo[k]) / P.lc[k]);
+    // cells are 3h (1 + 1e-9) or wider, so a product with 1/L_c instead of a
+    // quotient still leaves any pair closer than 3h in adjacent cells
+    double t = floor((xi[k] - P.lo[k]) * P.inv_lc[k]);
     int ci;
     if (!(t >= 0.0)) ci = 0;                       // also catches NaN
     else if (t >= double(P.nc[k])) ci = P.nc[k] - 1;
@@ -279,7 +281,7 @@ __global__ void __launch_bounds__(256) k_build(State S) {
           cn[k] = v;
         }
         if (skip) continue;
-        const unsigned code = unsigned((ox + 1) + 3 * (oy + 1) + 9 * (oz + 1));
+        const unsigned code = stencil_code(ox, oy, oz);
         const float fx = pi.x - float(ox) * lx, fy = pi.y - float(oy) * ly, fz = pi.z - float(oz) * lz;
         long long m = cell_key<DIM>(P, cn);
         for (int kind = 0; kind < 2; ++kind) {

@@ -16,20 +16,19 @@ struct Geo {
     if constexpr (MX) {
       pi = S.pf4[i];
     } else {
-_Pragma("unroll")
-      for (int k = 0; k < DIM; ++k) xi[k] = S.x[k][i];
+      _Pragma("unroll") for (int k = 0; k < DIM; ++k) xi[k] = S.x[k][i];
     }
   }
-  __device__ __forceinline__ R pair(const State &S, const CaseDev &P, unsigned e, int &j, R d[3]) const {
+  __device__ __forceinline__ R pair(const State &S, const CaseDev &P, const float lc[3], unsigned e,
+                                    int &j, R d[3]) const {
     j = int(e & kIdxMask);
     if constexpr (MX) {
       float4 pj = S.pf4[j];
-      return pair_f<DIM>(P, pi, pj, e >> kCodeShift, d);
+      return pair_f<DIM>(lc, pi, pj, e >> kCodeShift, d);
     } else {
       double dd[3];
       double r2 = pair_d<DIM>(P, xi, S.x, j, dd);
-_Pragma("unroll")
-      for (int k = 0; k < DIM; ++k) d[k] = dd[k];
+      _Pragma("unroll") for (int k = 0; k < DIM; ++k) d[k] = dd[k];
       if (DIM == 2) d[2] = 0.0;
       return r2;
     }
@@ -86,16 +85,18 @@ __global__ void k_density(State S) {
   int i = t.beg + threadIdx.x;
   if (i >= t.end) return;
   const CaseDev &P = S.cases[t.c];
+  KC<R> K;
+  K.set(P, P.h, P.inv_h, P.sig_h);
   Geo<DIM, MX> G;
   G.init(S, i);
-  const R sig = R(P.sig_h), ih = R(P.inv_h);
   R acc = R(0);
   ROW_LOOP(S, i, {
     int j;
     R d[3];
-    R r2 = G.pair(S, P, e, j, d);
-    acc += mass<MX>(S, j) * sig * poly_w<R>(qof<R>(sqrt_r(r2), P.h, P.inv_h));
+    R r2 = G.pair(S, P, K.lc, e, j, d);
+    acc += mass<MX>(S, j) * poly_w<R>(qof<R>(sqrt_r(r2), K.h, K.ih));
   })
+  acc *= K.sig;
   S.rho[i] = double(acc);
   if constexpr (MX) S.vf4[i].w = float(acc);
 }
@@ -124,20 +125,17 @@ __global__ void k_normals(State S, int pass) {
       double vj = S.m[j] / S.rho[j];
       if (pass == 0) {
         double fr = r > 0.0 ? P.sig_h * P.inv_h * poly_dw<double>(r / P.h) / r : 0.0;
-_Pragma("unroll")
-        for (int k = 0; k < DIM; ++k) acc[k] -= vj * fr * d[k];
+        _Pragma("unroll") for (int k = 0; k < DIM; ++k) acc[k] -= vj * fr * d[k];
       } else {
         double w = vj * P.sig_h * poly_w<double>(r / P.h);
-_Pragma("unroll")
-        for (int k = 0; k < DIM; ++k) acc[k] += w * S.nstar[k][j];
+        _Pragma("unroll") for (int k = 0; k < DIM; ++k) acc[k] += w * S.nstar[k][j];
       }
     }
   })
   double mag = sqrt(acc[0] * acc[0] + acc[1] * acc[1] + acc[2] * acc[2]);
   double thr = pass == 0 ? 1.0 / (4.0 * P.h) : 1e-6;
   bool keep = pass == 0 ? !(mag < thr) : (mag > thr);
-_Pragma("unroll")
-  for (int k = 0; k < 3; ++k) {
+  _Pragma("unroll") for (int k = 0; k < 3; ++k) {
     double v = keep ? acc[k] / mag : 0.0;
     if (pass == 0) S.nstar[k][i] = v;
     else S.nrm[k][i] = v;
@@ -160,8 +158,9 @@ __global__ void k_ghost(State S, int slip_stage) {
   if (i >= t.end) return;
   const CaseDev &P = S.cases[t.c];
   const bool slip = slip_stage && P.ustar_slip;
-  const R sig = R(slip ? P.sig_h : P.sig_h2);
-  const double hk = slip ? P.h : P.h2, ih = slip ? P.inv_h : P.inv_h2;
+  KC<R> K;
+  if (slip) K.set(P, P.h, P.inv_h, P.sig_h);
+  else K.set(P, P.h2, P.inv_h2, P.sig_h2);
   Geo<DIM, MX> G;
   G.init(S, i);
   R sw = R(0), su[3] = {R(0), R(0), R(0)};
@@ -170,35 +169,29 @@ __global__ void k_ghost(State S, int slip_stage) {
     int j = int(e & kIdxMask);
     if (j < fend) {
       R d[3];
-      R r2 = G.pair(S, P, e, j, d);
-      R w = sig * poly_w<R>(qof<R>(sqrt_r(r2), hk, ih));
+      R r2 = G.pair(S, P, K.lc, e, j, d);
+      R w = poly_w<R>(qof<R>(sqrt_r(r2), K.h, K.ih));
       R uj[3];
       vel<DIM, MX>(S, j, uj);
       sw += w;
-_Pragma("unroll")
-      for (int k = 0; k < DIM; ++k) su[k] += uj[k] * w;
+      _Pragma("unroll") for (int k = 0; k < DIM; ++k) su[k] += uj[k] * w;
     }
   })
   double ug[3] = {0, 0, 0}, nn[3] = {0, 0, 0}, ut[3];
-_Pragma("unroll")
-  for (int k = 0; k < DIM; ++k) {
+  _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
     ut[k] = sw > R(0) ? double(su[k]) / double(sw) : S.uw[k][i];
     nn[k] = S.nrm[k][i];
   }
   if (slip) {
-_Pragma("unroll")
-    for (int k = 0; k < DIM; ++k) ug[k] = ut[k];
+    _Pragma("unroll") for (int k = 0; k < DIM; ++k) ug[k] = ut[k];
   } else {
-_Pragma("unroll")
-    for (int k = 0; k < DIM; ++k) ug[k] = 2.0 * S.uw[k][i] - ut[k];
+    _Pragma("unroll") for (int k = 0; k < DIM; ++k) ug[k] = 2.0 * S.uw[k][i] - ut[k];
     double un = ug[0] * nn[0] + ug[1] * nn[1] + ug[2] * nn[2];
     if (un < 0.0) {
-_Pragma("unroll")
-      for (int k = 0; k < DIM; ++k) ug[k] -= un * nn[k];
+      _Pragma("unroll") for (int k = 0; k < DIM; ++k) ug[k] -= un * nn[k];
     }
   }
-_Pragma("unroll")
-  for (int k = 0; k < DIM; ++k) S.u[k][i] = ug[k];
+  _Pragma("unroll") for (int k = 0; k < DIM; ++k) S.u[k][i] = ug[k];
   if constexpr (MX) {
     float4 v = S.vf4[i];
     v.x = float(ug[0]); v.y = float(ug[1]); v.z = float(ug[2]);
@@ -224,66 +217,60 @@ __global__ void k_stage1(State S) {
   int i = t.beg + threadIdx.x;
   if (i >= t.end) return;
   const CaseDev &P = S.cases[t.c];
+  KC<R> K;
+  K.set(P, P.h, P.inv_h, P.sig_h);
   Geo<DIM, MX> G;
   G.init(S, i);
-  const R sig = R(P.sig_h), ih = R(P.inv_h);
-  const R dsc = sig * ih;
   const R nu4 = R(4.0 * P.nu), eh2 = R(P.eh2);
-  const R avc = R(P.alpha * P.h * P.c0);
+  const R avc = R(2.0 * P.alpha * P.h * P.c0);     // 2 alpha h c
   const bool av = P.alpha > 0.0;
   const int fend = P.fbeg + P.nf;
   R ui[3], uti[3];
   vel<DIM, MX>(S, i, ui);
   tvel<DIM, MX>(S, i, uti);
   const R ri = dens<MX>(S, i);
+  const R iri = R(1) / ri;
   R dti[3];
-_Pragma("unroll")
-  for (int k = 0; k < 3; ++k) dti[k] = uti[k] - ui[k];
+  _Pragma("unroll") for (int k = 0; k < 3; ++k) dti[k] = uti[k] - ui[k];
   R f[3] = {R(0), R(0), R(0)};
   ROW_LOOP(S, i, {
     int j;
     R d[3];
-    R r2 = G.pair(S, P, e, j, d);
+    R r2 = G.pair(S, P, K.lc, e, j, d);
     if (j != i) {
       R r = sqrt_r(r2);
-      R dw = dsc * poly_dw<R>(qof<R>(r, P.h, P.inv_h));
-      R fr = r > R(0) ? dw / r : R(0);
+      R dw = K.dsc * poly_dw<R>(qof<R>(r, K.h, K.ih));
+      R fr = r > R(0) ? divr(dw, r) : R(0);
       R rj = dens<MX>(S, j), mj = mass<MX>(S, j);
       R uj[3];
       vel<DIM, MX>(S, j, uj);
       R uij[3] = {ui[0] - uj[0], ui[1] - uj[1], ui[2] - uj[2]};
-      R rdw = fr * r2;
-      R visc = mj * nu4 / (ri + rj) * rdw / (r2 + eh2);
+      R rsum = ri + rj, reta = r2 + eh2;
+      R visc = divr(mj * nu4 * fr * r2, rsum * reta);
       R coef = R(0);
       if (av) {
         R vr = uij[0] * d[0] + uij[1] * d[1] + (DIM == 3 ? uij[2] * d[2] : R(0));
-        if (vr < R(0)) {
-          R phi = vr / (r2 + eh2);
-          R pij = -avc * phi / (R(0.5) * (ri + rj));
-          coef -= mj * pij;
-        }
+        // -m_j Pi_ij = m_j alpha h c phi_ij / ((rho_i + rho_j)/2)
+        if (vr < R(0)) coef = divr(mj * avc * vr, reta * rsum);
       }
       R ai = R(0), aj = R(0);
       if (j < fend) {
         R utj[3];
         tvel<DIM, MX>(S, j, utj);
         R gi = R(0), gj = R(0);
-_Pragma("unroll")
-        for (int k = 0; k < DIM; ++k) {
+        _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
           gi += dti[k] * d[k];
           gj += (utj[k] - uj[k]) * d[k];
         }
-        ai = mj * fr * gi / ri;
-        aj = mj * fr * gj / rj;
+        ai = mj * fr * gi * iri;
+        aj = divr(mj * fr * gj, rj);
       }
-_Pragma("unroll")
-      for (int k = 0; k < DIM; ++k)
+      _Pragma("unroll") for (int k = 0; k < DIM; ++k)
         f[k] += visc * uij[k] + coef * fr * d[k] + ui[k] * ai + uj[k] * aj;
     }
   })
   const double dt = P.dt;
-_Pragma("unroll")
-  for (int k = 0; k < DIM; ++k) {
+  _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
     double fk = double(f[k]) + P.g[k];
     S.us[k][i] = S.u[k][i] + dt * fk;
     double xk = __dadd_rn(S.x[k][i], __dmul_rn(dt, S.ut[k][i]));
@@ -321,35 +308,35 @@ __global__ void k_pgrad(State S) {
   int i = t.beg + threadIdx.x;
   if (i >= t.end) return;
   const CaseDev &P = S.cases[t.c];
+  KC<R> K;
+  K.set(P, P.h, P.inv_h, P.sig_h);
   Geo<DIM, MX> G;
   G.init(S, i);
-  const R dsc = R(P.sig_h * P.inv_h), ih = R(P.inv_h);
   const R ri = dens<MX>(S, i);
   R pi;
   if constexpr (MX) pi = S.pf[i];
   else pi = S.p[i];
-  const R pri = pi / (ri * ri);
+  const R pri = divr(pi, ri * ri);
+  const R iri = R(1) / ri;
   R f[3] = {R(0), R(0), R(0)};
   const bool symm = P.pgrad_symm != 0;
   ROW_LOOP(S, i, {
     int j;
     R d[3];
-    R r2 = G.pair(S, P, e, j, d);
+    R r2 = G.pair(S, P, K.lc, e, j, d);
     if (j != i) {
       R r = sqrt_r(r2);
-      R fr = r > R(0) ? dsc * poly_dw<R>(qof<R>(r, P.h, P.inv_h)) / r : R(0);
+      R fr = r > R(0) ? divr(K.dsc * poly_dw<R>(qof<R>(r, K.h, K.ih)), r) : R(0);
       R rj = dens<MX>(S, j), mj = mass<MX>(S, j);
       R pj;
       if constexpr (MX) pj = S.pf[j];
       else pj = S.p[j];
-      R c = symm ? -mj * (pri + pj / (rj * rj)) : -mj / (ri * rj) * (pj - pi);
+      R c = symm ? -mj * (pri + divr(pj, rj * rj)) : -divr(mj * (pj - pi), rj) * iri;
       c *= fr;
-_Pragma("unroll")
-      for (int k = 0; k < DIM; ++k) f[k] += c * d[k];
+      _Pragma("unroll") for (int k = 0; k < DIM; ++k) f[k] += c * d[k];
     }
   })
-_Pragma("unroll")
-  for (int k = 0; k < DIM; ++k) S.u[k][i] = S.u[k][i] + P.dt * double(f[k]);
+  _Pragma("unroll") for (int k = 0; k < DIM; ++k) S.u[k][i] = S.u[k][i] + P.dt * double(f[k]);
 }
 
 // p_ref = 2 max_i p_i after the first PPE solve (internal flows, Sec. 2.1);
@@ -380,16 +367,17 @@ __global__ void k_pref(State S) {
 //   p0_i = p_ref, or min(10|p_i|, p_ref) for external flows.
 // ---------------------------------------------------------------------------
 template <int DIM, bool MX>
-__global__ void k_gtvf(State S, int sub, int cur) {
+__global__ void k_gtvf(State S, int sub, int cur, int skip_k1) {
   using R = typename Geo<DIM, MX>::R;
   const Tile &t = S.ftiles[blockIdx.x];
   int i = t.beg + threadIdx.x;
   if (i >= t.end) return;
   const CaseDev &P = S.cases[t.c];
-  if (sub >= P.K) return;
+  if (sub >= P.K || (skip_k1 && P.K == 1)) return;
+  KC<R> K;
+  K.set(P, P.hg, P.inv_hg, P.sig_hg);
   Geo<DIM, MX> G;
   G.init(S, i);
-  const R dsc = R(P.sig_hg * P.inv_hg), ih = R(P.inv_hg);
   const int fend = P.fbeg + P.nf;
   R di[3] = {R(0), R(0), R(0)};
   if (sub > 0) {
@@ -397,15 +385,14 @@ __global__ void k_gtvf(State S, int sub, int cur) {
       float4 v = S.dgf[cur][i];
       di[0] = v.x; di[1] = v.y; di[2] = v.z;
     } else {
-_Pragma("unroll")
-      for (int k = 0; k < DIM; ++k) di[k] = S.dg[cur][k][i];
+      _Pragma("unroll") for (int k = 0; k < DIM; ++k) di[k] = S.dg[cur][k][i];
     }
   }
   R acc[3] = {R(0), R(0), R(0)};
   ROW_LOOP(S, i, {
     int j;
     R d[3];
-    G.pair(S, P, e, j, d);
+    G.pair(S, P, K.lc, e, j, d);
     if (j != i) {
       if (sub > 0 && j < fend) {
         R dj[3];
@@ -413,20 +400,17 @@ _Pragma("unroll")
           float4 v = S.dgf[cur][j];
           dj[0] = v.x; dj[1] = v.y; dj[2] = v.z;
         } else {
-_Pragma("unroll")
-          for (int k = 0; k < DIM; ++k) dj[k] = S.dg[cur][k][j];
+          _Pragma("unroll") for (int k = 0; k < DIM; ++k) dj[k] = S.dg[cur][k][j];
         }
-_Pragma("unroll")
-        for (int k = 0; k < DIM; ++k) d[k] += di[k] - dj[k];
+        _Pragma("unroll") for (int k = 0; k < DIM; ++k) d[k] += di[k] - dj[k];
       }
       R r2 = d[0] * d[0] + d[1] * d[1] + (DIM == 3 ? d[2] * d[2] : R(0));
       R r = sqrt_r(r2);
       if (r > R(0)) {
-        R fr = dsc * poly_dw<R>(qof<R>(r, P.hg, P.inv_hg)) / r;
+        R fr = divr(K.dsc * poly_dw<R>(qof<R>(r, K.h, K.ih)), r);
         R rj = dens<MX>(S, j);
-        R c = mass<MX>(S, j) / (rj * rj) * fr;
-_Pragma("unroll")
-        for (int k = 0; k < DIM; ++k) acc[k] += c * d[k];
+        R c = divr(mass<MX>(S, j), rj * rj) * fr;
+        _Pragma("unroll") for (int k = 0; k < DIM; ++k) acc[k] += c * d[k];
       }
     }
   })
@@ -436,12 +420,10 @@ _Pragma("unroll")
   const double dtau = P.dt / P.K;
   const int nxt = cur ^ 1;
   double dn[3] = {0, 0, 0};
-_Pragma("unroll")
-  for (int k = 0; k < DIM; ++k) {
+  _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
     double fk = -p0 * double(acc[k]);
     double vk = sub > 0 ? S.vgt[k][i] : 0.0;
     double dk = sub > 0 ? double(di[k]) : 0.0;
-    if constexpr (!MX) dk = sub > 0 ? S.dg[cur][k][i] : 0.0;
     dn[k] = dk + dtau * vk + 0.5 * dtau * dtau * fk;
     S.vgt[k][i] = vk + dtau * fk;
     if constexpr (!MX) S.dg[nxt][k][i] = dn[k];
@@ -450,17 +432,90 @@ _Pragma("unroll")
 }
 
 // ---------------------------------------------------------------------------
-// Eqs. int:vhatnp2, int:rnp2:  u~^{n+1} = u^{n+1} + (r^K - r^0)/dt,
-//   r^{n+1} = r^n + dt (u~^{n+1} + u~^n)/2, wrapped into periodic boxes.
+// MIXED form, one pass over the r* lists for a case with one GTVF sub-step:
+// pressure gradient and correction (Eq. int:vnp1), the GTVF force at r*
+// (Eq. mom:sph:gtvf) and, with K = 1, d = dt^2/2 f (Eq. int:gtvf:pos),
+// then the transport velocity and position update (Eqs. int:vhatnp2,
+// int:rnp2).  Neighbours are read only through the FP32 mirrors (positions,
+// mass, density, pressure), which this pass does not write, so the in-place
+// FP64 updates of u, u~ and r cannot race.  A tile of a case with K > 1 only
+// takes the pressure gradient here; its GTVF and update run as separate passes.
 // ---------------------------------------------------------------------------
-template <int DIM, bool MX>
-__global__ void k_update(State S, int fin) {
+template <int DIM>
+__global__ void k_pgrad_gtvf1(State S) {
   const Tile &t = S.ftiles[blockIdx.x];
   int i = t.beg + threadIdx.x;
   if (i >= t.end) return;
   const CaseDev &P = S.cases[t.c];
+  const bool fused = P.K == 1;
+  KC<float> K, KG;
+  K.set(P, P.h, P.inv_h, P.sig_h);
+  KG.set(P, P.hg, P.inv_hg, P.sig_hg);
+  const float4 pi4 = S.pf4[i];
+  const float ri = S.vf4[i].w;
+  const float pi = S.pf[i];
+  const float pri = divr(pi, ri * ri);
+  const float iri = 1.f / ri;
+  const bool symm = P.pgrad_symm != 0;
+  float f[3] = {0.f, 0.f, 0.f}, acc[3] = {0.f, 0.f, 0.f};
+  ROW_LOOP(S, i, {
+    const int j = int(e & kIdxMask);
+    if (j != i) {
+      float4 pj4 = S.pf4[j];
+      float d[3];
+      float r2 = pair_f<DIM>(K.lc, pi4, pj4, e >> kCodeShift, d);
+      float r = sqrtf(r2);
+      float rj = S.vf4[j].w, mj = pj4.w, pj = S.pf[j];
+      float fr = r > 0.f ? divr(K.dsc * poly_dw<float>(qof<float>(r, K.h, K.ih)), r) : 0.f;
+      float c = symm ? -mj * (pri + divr(pj, rj * rj)) : -divr(mj * (pj - pi), rj) * iri;
+      c *= fr;
+      _Pragma("unroll") for (int k = 0; k < DIM; ++k) f[k] += c * d[k];
+      if (fused && r > 0.f) {
+        float frg = divr(KG.dsc * poly_dw<float>(qof<float>(r, KG.h, KG.ih)), r);
+        float cg = divr(mj, rj * rj) * frg;
+        _Pragma("unroll") for (int k = 0; k < DIM; ++k) acc[k] += cg * d[k];
+      }
+    }
+  })
+  const double dt = P.dt;
+  double unew[3] = {0, 0, 0};
+  _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
+    unew[k] = S.u[k][i] + dt * double(f[k]);
+    S.u[k][i] = unew[k];
+  }
+  if (!fused) return;
+  const double pref = S.pref[t.c];
+  const double p0 = P.pref_mode == SISPH_PREF_EXTERNAL ? fmin(10.0 * fabs(S.p[i]), pref) : pref;
+  double dn[3] = {0, 0, 0};
+  _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
+    double fk = -p0 * double(acc[k]);
+    dn[k] = 0.5 * dt * dt * fk;
+    S.vgt[k][i] = dt * fk;
+    double old = S.ut[k][i];
+    double nw = __dadd_rn(unew[k], __ddiv_rn(double(float(dn[k])), dt));
+    double xk = __dadd_rn(S.xn[k][i], __dmul_rn(__dmul_rn(0.5, dt), __dadd_rn(nw, old)));
+    if (P.per[k]) {
+      if (xk >= P.hi[k]) xk -= P.L[k];
+      else if (xk < P.lo[k]) xk += P.L[k];
+    }
+    S.x[k][i] = xk;
+    S.ut[k][i] = nw;
+  }
+  S.dgf[1][i] = make_float4(float(dn[0]), float(dn[1]), float(dn[2]), 0.f);
+}
+
+// ---------------------------------------------------------------------------
+// Eqs. int:vhatnp2, int:rnp2:  u~^{n+1} = u^{n+1} + (r^K - r^0)/dt,
+//   r^{n+1} = r^n + dt (u~^{n+1} + u~^n)/2, wrapped into periodic boxes.
+// ---------------------------------------------------------------------------
+template <int DIM, bool MX>
+__global__ void k_update(State S, int skip_k1) {
+  const Tile &t = S.ftiles[blockIdx.x];
+  int i = t.beg + threadIdx.x;
+  if (i >= t.end) return;
+  const CaseDev &P = S.cases[t.c];
+  if (skip_k1 && P.K == 1) return;
   const int par = P.K > 0 ? (P.K & 1) : 0;
-  (void)fin;
   const double dt = P.dt;
   float4 df = make_float4(0.f, 0.f, 0.f, 0.f);
   if constexpr (MX) df = S.dgf[par][i];
@@ -574,19 +629,29 @@ cudaError_t launch_pref(const State &S, const Launch &L) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_gtvf(const State &S, const Launch &L, int kmax) {
+cudaError_t launch_gtvf(const State &S, const Launch &L, int kmax, int skip_k1) {
   if (S.nft == 0) return cudaSuccess;
   if (L.before) L.before(L.ctx, "gtvf");
-  for (int sub = 0; sub < kmax; ++sub) DISPATCH(S, k_gtvf, <<<S.nft, S.T, 0, L.stream>>>(S, sub, sub & 1));
+  for (int sub = 0; sub < kmax; ++sub)
+    DISPATCH(S, k_gtvf, <<<S.nft, S.T, 0, L.stream>>>(S, sub, sub & 1, skip_k1));
   if (L.after) L.after(L.ctx, "gtvf", double(S.nf) * kmax, kmax);
   return cudaGetLastError();
 }
 
-cudaError_t launch_update(const State &S, const Launch &L) {
+cudaError_t launch_update(const State &S, const Launch &L, int skip_k1) {
   if (S.nft == 0) return cudaSuccess;
   if (L.before) L.before(L.ctx, "update");
-  DISPATCH(S, k_update, <<<S.nft, S.T, 0, L.stream>>>(S, 0));
+  DISPATCH(S, k_update, <<<S.nft, S.T, 0, L.stream>>>(S, skip_k1));
   if (L.after) L.after(L.ctx, "update", double(S.nf), 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pgrad_gtvf1(const State &S, const Launch &L) {
+  if (S.nft == 0) return cudaSuccess;
+  if (L.before) L.before(L.ctx, "pgrad_gtvf");
+  if (S.dim == 2) k_pgrad_gtvf1<2><<<S.nft, S.T, 0, L.stream>>>(S);
+  else k_pgrad_gtvf1<3><<<S.nft, S.T, 0, L.stream>>>(S);
+  if (L.after) L.after(L.ctx, "pgrad_gtvf", double(S.nf), 1);
   return cudaGetLastError();
 }
 

@@ -36,6 +36,8 @@ __global__ void k_setup_fluid(State S) {
   const CaseDev &P = S.cases[t.c];
   double lam = 0.0;
   if (i < t.end) {
+    KC<R> K;
+    K.set(P, P.h, P.inv_h, P.sig_h);
     double xi[3] = {0, 0, 0};
     float4 pi4 = make_float4(0.f, 0.f, 0.f, 0.f);
     R ri, ui[3];
@@ -44,18 +46,18 @@ __global__ void k_setup_fluid(State S) {
       float4 v = S.vf4[i];
       ri = v.w; ui[0] = v.x; ui[1] = v.y; ui[2] = v.z;
     } else {
-#pragma unroll
-      for (int k = 0; k < DIM; ++k) { xi[k] = S.x[k][i]; ui[k] = S.u[k][i]; }
+      _Pragma("unroll") for (int k = 0; k < DIM; ++k) { xi[k] = S.x[k][i]; ui[k] = S.u[k][i]; }
       if (DIM == 2) ui[2] = 0.0;
       ri = S.rho[i];
     }
-    const R dsc = R(P.sig_h * P.inv_h), ih = R(P.inv_h), eh2 = R(P.eh2);
+    const R eh2 = R(P.eh2);
     const R idt = R(1.0 / P.dt);
+    const R four_iri = R(4) / ri;
     R rhs = R(0), rc = R(0), dg = R(0), dc = R(0);
     const int cnt = S.ncnt[i];
     const long long n = S.n;
     R *coef = static_cast<R *>(S.coef);
-    for (int k = 0; k < cnt; ++k) {
+    _Pragma("unroll 4") for (int k = 0; k < cnt; ++k) {
       unsigned e = S.nbr[(long long)k * n + i];
       int j = int(e & kIdxMask);
       R fac = R(0);
@@ -63,26 +65,24 @@ __global__ void k_setup_fluid(State S) {
         R d[3], r2, rj, mj, uj[3];
         if constexpr (MX) {
           float4 pj = S.pf4[j];
-          r2 = pair_f<DIM>(P, pi4, pj, e >> kCodeShift, d);
+          r2 = pair_f<DIM>(K.lc, pi4, pj, e >> kCodeShift, d);
           float4 v = S.vf4[j];
           rj = v.w; uj[0] = v.x; uj[1] = v.y; uj[2] = v.z;
           mj = pj.w;
         } else {
           double dd[3];
           r2 = pair_d<DIM>(P, xi, S.x, j, dd);
-#pragma unroll
-          for (int q = 0; q < DIM; ++q) { d[q] = dd[q]; uj[q] = S.u[q][j]; }
+          _Pragma("unroll") for (int q = 0; q < DIM; ++q) { d[q] = dd[q]; uj[q] = S.u[q][j]; }
           if (DIM == 2) { d[2] = 0.0; uj[2] = 0.0; }
           rj = S.rho[j];
           mj = S.m[j];
         }
         R r = sqrt_r(r2);
-        R fr = r > R(0) ? dsc * poly_dw<R>(qof<R>(r, P.h, P.inv_h)) / r : R(0);
+        R fr = r > R(0) ? divr(K.dsc * poly_dw<R>(qof<R>(r, K.h, K.ih)), r) : R(0);
         R ud = R(0);
-#pragma unroll
-        for (int q = 0; q < DIM; ++q) ud += (ui[q] - uj[q]) * d[q];
-        R src = -(mj / rj) * idt * fr * ud;
-        fac = R(4) * mj / (ri * (ri + rj)) * (fr * r2) / (r2 + eh2);
+        _Pragma("unroll") for (int q = 0; q < DIM; ++q) ud += (ui[q] - uj[q]) * d[q];
+        R src = -divr(mj * idt * fr * ud, rj);
+        fac = divr(four_iri * mj * (fr * r2), (ri + rj) * (r2 + eh2));
         if constexpr (MX) {
           kahan_add(rhs, rc, src);
           kahan_add(dg, dc, fac);
@@ -131,16 +131,16 @@ __global__ void k_setup_wall(State S) {
   int i = t.beg + threadIdx.x;
   if (i >= t.end) return;
   const CaseDev &P = S.cases[t.c];
+  KC<R> K;
+  K.set(P, P.h, P.inv_h, P.sig_h);
   const int r = P.wrow + (i - P.wbeg);
   const int fend = P.fbeg + P.nf;
   double xi[3] = {0, 0, 0};
   float4 pi4 = make_float4(0.f, 0.f, 0.f, 0.f);
   if constexpr (MX) pi4 = S.pf4[i];
   else {
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) xi[k] = S.x[k][i];
+    _Pragma("unroll") for (int k = 0; k < DIM; ++k) xi[k] = S.x[k][i];
   }
-  const R sig = R(P.sig_h), ih = R(P.inv_h);
   R sw = R(0), acc[3] = {R(0), R(0), R(0)};
   int cnt = 0;
   const int cnti = S.ncnt[i];
@@ -153,27 +153,24 @@ __global__ void k_setup_wall(State S) {
     R d[3], r2, rj;
     if constexpr (MX) {
       float4 pj = S.pf4[j];
-      r2 = pair_f<DIM>(P, pi4, pj, e >> kCodeShift, d);
+      r2 = pair_f<DIM>(K.lc, pi4, pj, e >> kCodeShift, d);
       rj = S.vf4[j].w;
     } else {
       double dd[3];
       r2 = pair_d<DIM>(P, xi, S.x, j, dd);
-#pragma unroll
-      for (int q = 0; q < DIM; ++q) d[q] = dd[q];
+      _Pragma("unroll") for (int q = 0; q < DIM; ++q) d[q] = dd[q];
       if (DIM == 2) d[2] = 0.0;
       rj = S.rho[j];
     }
-    R w = sig * poly_w<R>(qof<R>(sqrt_r(r2), P.h, P.inv_h));
+    R w = K.sig * poly_w<R>(qof<R>(sqrt_r(r2), K.h, K.ih));
     S.widx[(long long)cnt * nw + r] = j;
     wc[(long long)cnt * nw + r] = w;
     ++cnt;
     sw += w;
-#pragma unroll
-    for (int q = 0; q < DIM; ++q) acc[q] += rj * d[q] * w;
+    _Pragma("unroll") for (int q = 0; q < DIM; ++q) acc[q] += rj * d[q] * w;
   }
   R hw = R(0);
-#pragma unroll
-  for (int q = 0; q < DIM; ++q) hw += R(P.g[q]) * acc[q];
+  _Pragma("unroll") for (int q = 0; q < DIM; ++q) hw += R(P.g[q]) * acc[q];
   S.wcnt[r] = cnt;
   static_cast<R *>(S.wsinv)[r] = sw > R(0) ? R(1) / sw : R(0);
   static_cast<R *>(S.wh)[r] = hw;
@@ -215,6 +212,24 @@ __device__ __forceinline__ bool grid_sync(Barrier *b, unsigned nblocks, long lon
   }
   __syncthreads();
   return ok != 0;
+}
+
+__device__ __forceinline__ void block_sum2f(float &a, float &b, double *sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  float *shf = reinterpret_cast<float *>(sh);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) { shf[w] = a; shf[32 + w] = b; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float sa = 0.f, sb = 0.f;
+    for (int q = 0; q < nw; ++q) { sa += shf[q]; sb += shf[32 + q]; }
+    a = sa;
+    b = sb;
+  }
 }
 
 __device__ __forceinline__ void block_sum2(double &a, double &b, double *sh) {
@@ -316,21 +331,42 @@ __global__ void __launch_bounds__(256) k_sweeps(State S) {
       if (__ldcg(done + t.c)) continue;
       int i = t.beg + threadIdx.x;
       double dn = 0.0, dp = 0.0;
+      R dnr = R(0), dpr = R(0);
       if (i < t.end) {
         R acc = prhs[i];
-        int cnt = S.ncnt[i];
-        _Pragma("unroll 4") for (int q = 0; q < cnt; ++q) {
-          long long o = (long long)q * n + i;
-          unsigned e = S.nbr[o];
-          acc += coef[o] * pc[e & kIdxMask];
+        const int cnt = S.ncnt[i];
+        // chunks of 8 slots: 8 independent index/coefficient loads, then 8
+        // independent gathers, so a row costs a few memory round trips
+        for (int q0 = 0; q0 < cnt; q0 += 8) {
+          unsigned e[8];
+          R cf[8];
+          _Pragma("unroll") for (int u = 0; u < 8; ++u) {
+            const int q = q0 + u;
+            const long long o = (long long)q * n + i;
+            e[u] = q < cnt ? S.nbr[o] : unsigned(i);
+            cf[u] = q < cnt ? coef[o] : R(0);
+          }
+          R pj[8];
+          _Pragma("unroll") for (int u = 0; u < 8; ++u) pj[u] = pc[e[u] & kIdxMask];
+          _Pragma("unroll") for (int u = 0; u < 8; ++u) acc += cf[u] * pj[u];
         }
         R po = pc[i];
         R pnew = pwd[i] * acc + om1 * po;
         pn[i] = pnew;
-        dn = fabs(double(pnew - po));
-        dp = fabs(double(pnew));
+        dnr = fabs(pnew - po);
+        dpr = fabs(pnew);
       }
-      block_sum2(dn, dp, sh);
+      // tile sums in the sweep's precision (256 terms), the sum over tiles
+      // and cases in FP64
+      if constexpr (MX) {
+        block_sum2f(dnr, dpr, sh);
+        dn = double(dnr);
+        dp = double(dpr);
+      } else {
+        dn = dnr;
+        dp = dpr;
+        block_sum2(dn, dp, sh);
+      }
       if (threadIdx.x == 0) {
         S.tile_part[2 * tt] = dn;
         S.tile_part[2 * tt + 1] = dp;

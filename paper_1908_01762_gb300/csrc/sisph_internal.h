@@ -17,7 +17,7 @@
 
 namespace sisph {
 
-constexpr int kCodeShift = 27;                   // neighbour entry = j | code << 27
+constexpr int kCodeShift = 26;                   // neighbour entry = j | code << 26
 constexpr unsigned kIdxMask = (1u << kCodeShift) - 1u;
 constexpr int kMaxParticles = (1 << kCodeShift) - 1;
 
@@ -30,7 +30,7 @@ constexpr int kErrNotConv = 8;    // a PPE solve stopped at max_iter
 struct CaseDev {
   // cell grid
   double lo[3], hi[3], L[3], half[3];
-  double lc[3];
+  double lc[3], inv_lc[3];
   float lcf[3];
   int nc[3];
   int per[3];
@@ -158,10 +158,27 @@ __host__ __device__ inline double quintic_sigma(double h, int dim) {
 // a pair within rounding of the support edge gets the same (zero or tiny)
 // weight as in a plain evaluation; the FP32 form multiplies by 1/h.
 template <typename R>
-__device__ __forceinline__ R qof(R r, double h, double inv_h) {
-  if constexpr (std::is_same<R, float>::value) return r * float(inv_h);
+__device__ __forceinline__ R qof(R r, R h, R inv_h) {
+  if constexpr (std::is_same<R, float>::value) return r * inv_h;
   else return r / h;
 }
+
+// Per-case constants of a neighbour pass, converted once per thread to the
+// pass's arithmetic type.
+template <typename R>
+struct KC {
+  R h, ih, sig, dsc;   // support h: q = r/h, W = sig poly_w(q), dW/dr = dsc poly_dw(q)
+  float lc[3];
+  __device__ __forceinline__ void set(const CaseDev &P, double h_, double ih_, double sig_) {
+    h = R(h_);
+    ih = R(ih_);
+    sig = R(sig_);
+    dsc = R(sig_ * ih_);
+    lc[0] = P.lcf[0];
+    lc[1] = P.lcf[1];
+    lc[2] = P.lcf[2];
+  }
+};
 
 template <typename R>
 __device__ __forceinline__ R sqrt_r(R v) {
@@ -189,24 +206,38 @@ __device__ __forceinline__ double pair_d(const CaseDev &P, const double xi[3],
   return r2;
 }
 
-// Pair vector from FP32 cell-relative positions: r_ij = rel_i - rel_j - o lc,
-// where o is the stencil offset (code) of j's cell seen from i's cell.
+// Stencil offset o in {-1,0,1}^3 of j's cell seen from i's cell, stored in
+// the top bits of a neighbour entry as 2 bits per axis: (o_x+1) | (o_y+1)<<2
+// | (o_z+1)<<4.
+__host__ __device__ __forceinline__ unsigned stencil_code(int ox, int oy, int oz) {
+  return unsigned(ox + 1) | (unsigned(oy + 1) << 2) | (unsigned(oz + 1) << 4);
+}
+
+// Pair vector from FP32 cell-relative positions: r_ij = rel_i - rel_j - o lc.
 template <int DIM>
-__device__ __forceinline__ float pair_f(const CaseDev &P, const float4 &pi, const float4 &pj,
+__device__ __forceinline__ float pair_f(const float lc[3], const float4 &pi, const float4 &pj,
                                         unsigned code, float d[3]) {
-  int ox = int(code % 3u) - 1;
-  int oy = int((code / 3u) % 3u) - 1;
-  d[0] = (pi.x - pj.x) - float(ox) * P.lcf[0];
-  d[1] = (pi.y - pj.y) - float(oy) * P.lcf[1];
+  const float ox = float(int(code & 3u) - 1);
+  const float oy = float(int((code >> 2) & 3u) - 1);
+  d[0] = (pi.x - pj.x) - ox * lc[0];
+  d[1] = (pi.y - pj.y) - oy * lc[1];
   float r2 = d[0] * d[0] + d[1] * d[1];
   if (DIM == 3) {
-    int oz = int(code / 9u) - 1;
-    d[2] = (pi.z - pj.z) - float(oz) * P.lcf[2];
+    const float oz = float(int(code >> 4) - 1);
+    d[2] = (pi.z - pj.z) - oz * lc[2];
     r2 += d[2] * d[2];
   } else {
     d[2] = 0.f;
   }
   return r2;
+}
+
+// a / b: exact in FP64; the fast approximate division (a few ulp) in FP32,
+// well inside the FP32 error budget of the MIXED form.
+template <typename R>
+__device__ __forceinline__ R divr(R a, R b) {
+  if constexpr (std::is_same<R, float>::value) return __fdividef(a, b);
+  else return a / b;
 }
 
 __device__ __forceinline__ void store_r(void *base, long long i, double v, int mixed) {
@@ -236,8 +267,9 @@ cudaError_t launch_ghost(const State &S, const Launch &L, int slip_stage);
 cudaError_t launch_stage1(const State &S, const Launch &L);
 cudaError_t launch_pgrad(const State &S, const Launch &L);
 cudaError_t launch_pref(const State &S, const Launch &L);
-cudaError_t launch_gtvf(const State &S, const Launch &L, int kmax);
-cudaError_t launch_update(const State &S, const Launch &L);
+cudaError_t launch_gtvf(const State &S, const Launch &L, int kmax, int skip_k1);
+cudaError_t launch_update(const State &S, const Launch &L, int skip_k1);
+cudaError_t launch_pgrad_gtvf1(const State &S, const Launch &L);
 cudaError_t launch_scatter_field(const State &S, const Launch &L, const void *src, int is_float,
                                  int stride_f4, int comp, double *dst_user);
 cudaError_t launch_gather_field(const State &S, const Launch &L, const double *src_user, double *dst);
