@@ -322,10 +322,13 @@ int setup_case(sisph_t s, int c, const sisph_particles &P, const sisph_case_para
       D.nc[k] = int(ncd);
       D.lc[k] = D.L[k] / double(D.nc[k]);
     } else {
+      // one margin cell on each side: particles inside [lo, hi) never sit in
+      // an edge cell, which only collects particles that left the box
       D.lc[k] = lcmin;
       double ncd = std::ceil(D.L[k] / lcmin);
       if (ncd > 1e6) return fail(nullptr, SISPH_EINVAL, "case " + std::to_string(c) + ": too many cells");
-      D.nc[k] = std::max(1, int(ncd));
+      D.nc[k] = std::max(1, int(ncd)) + 2;
+      D.lo[k] = P.lo[k] - lcmin;
     }
     D.lcf[k] = float(D.lc[k]);
     D.inv_lc[k] = 1.0 / D.lc[k];

@@ -240,15 +240,28 @@ __global__ void k_copy_static(State S) {
   for (int k = 0; k < 3; ++k) S.uw[k][i] = S.nstar[k][i];
 }
 
+// A cell on the edge of a non-periodic grid holds the particles that left
+// the box (clamped into it), whose cell-relative coordinates can be large.
+template <int DIM>
+__device__ __forceinline__ bool edge_cell(const CaseDev &P, const int c[3]) {
+  bool e = false;
+  _Pragma("unroll") for (int k = 0; k < DIM; ++k)
+    e |= !P.per[k] && (c[k] == 0 || c[k] == P.nc[k] - 1);
+  return e;
+}
+
 // One thread per particle: scan the 3^d stencil of cells (fluid block, then
 // wall block of each cell) and append every j with |r_ij|^2 < (3h)^2 to the
 // ELL row.  Each candidate is first tested in FP32 on cell-relative
-// coordinates; only pairs within a relative band of 1e-4 around the cutoff
-// (the FP32 error is below 1e-5 of (3h)^2 for positions inside their cell)
-// go to the exact unfused FP64 test, so the set equals the FP64 definition.
-// Particles clamped far outside a non-periodic box take the FP64 test always.
+// coordinates (error below 1e-5 of (3h)^2); a pair within a relative band of
+// 1e-4 around the cutoff is set aside and decided after the cell loop by the
+// exact unfused FP64 test, so the set equals the FP64 definition and a warp
+// pays for as many FP64 tests as its busiest lane (lattice inputs put many
+// pairs exactly on the cutoff).  Edge cells of a non-periodic grid take the
+// FP64 test directly.
 template <int DIM>
 __global__ void __launch_bounds__(256) k_build(State S) {
+  constexpr int kBand = DIM == 3 ? 48 : 16;
   const Tile &t = tile_of(S, blockIdx.x);
   int i = t.beg + threadIdx.x;
   if (i >= t.end) return;
@@ -256,16 +269,22 @@ __global__ void __launch_bounds__(256) k_build(State S) {
   double xi[3] = {S.x[0][i], S.x[1][i], DIM == 3 ? S.x[2][i] : 0.0};
   int c[3];
   cell_of<DIM>(P, xi, c);
+  const bool own_edge = edge_cell<DIM>(P, c);
   const float4 pi = S.pf4[i];
   const float lx = P.lcf[0], ly = P.lcf[1], lz = P.lcf[2];
-  const float lim = 1.5f * fmaxf(lx, fmaxf(ly, DIM == 3 ? lz : ly));
-  const bool out_i = fabsf(pi.x) > lim || fabsf(pi.y) > lim || (DIM == 3 && fabsf(pi.z) > lim);
   const float cut2f = float(P.cut2);
   const float lo_band = cut2f * (1.0f - 1e-4f), hi_band = cut2f * (1.0f + 1e-4f);
   const int zr = (DIM == 3) ? 1 : 0;
   int cnt = 0;
   bool over = false;
   const long long nn = S.n;
+  unsigned band[kBand];
+  int nband = 0;
+  auto append = [&](unsigned entry) {
+    if (cnt < S.cap) S.nbr[(long long)cnt * nn + i] = entry;
+    else over = true;
+    ++cnt;
+  };
   for (int oz = -zr; oz <= zr; ++oz) {
     for (int oy = -1; oy <= 1; ++oy) {
       for (int ox = -1; ox <= 1; ++ox) {
@@ -281,7 +300,8 @@ __global__ void __launch_bounds__(256) k_build(State S) {
           cn[k] = v;
         }
         if (skip) continue;
-        const unsigned code = stencil_code(ox, oy, oz);
+        const bool exact_all = own_edge || edge_cell<DIM>(P, cn);
+        const unsigned code = stencil_code(ox, oy, oz) << kCodeShift;
         const float fx = pi.x - float(ox) * lx, fy = pi.y - float(oy) * ly, fz = pi.z - float(oz) * lz;
         long long m = cell_key<DIM>(P, cn);
         for (int kind = 0; kind < 2; ++kind) {
@@ -289,6 +309,11 @@ __global__ void __launch_bounds__(256) k_build(State S) {
           long long q = P.key_base + (long long)kind * P.slots + m;
           unsigned beg = S.hist[q], end = S.hist[q + 1];
           for (unsigned j = beg; j < end; ++j) {
+            if (exact_all) {
+              double d[3];
+              if (pair_d<DIM>(P, xi, S.x, int(j), d) < P.cut2) append(j | code);
+              continue;
+            }
             float4 pj = S.pf4[j];
             float dx = fx - pj.x, dy = fy - pj.y;
             float r2f = dx * dx + dy * dy;
@@ -296,23 +321,24 @@ __global__ void __launch_bounds__(256) k_build(State S) {
               float dz = fz - pj.z;
               r2f += dz * dz;
             }
-            bool in;
-            bool out_j = fabsf(pj.x) > lim || fabsf(pj.y) > lim || (DIM == 3 && fabsf(pj.z) > lim);
-            if (!out_i && !out_j && r2f < lo_band) in = true;
-            else if (!out_i && !out_j && r2f > hi_band) in = false;
-            else {
-              double d[3];
-              in = pair_d<DIM>(P, xi, S.x, int(j), d) < P.cut2;
-            }
-            if (in) {
-              if (cnt < S.cap) S.nbr[(long long)cnt * nn + i] = j | (code << kCodeShift);
-              else over = true;
-              ++cnt;
+            if (r2f < lo_band) {
+              append(j | code);
+            } else if (r2f <= hi_band) {
+              if (nband < kBand) {
+                band[nband++] = j | code;
+              } else {
+                double d[3];
+                if (pair_d<DIM>(P, xi, S.x, int(j), d) < P.cut2) append(j | code);
+              }
             }
           }
         }
       }
     }
+  }
+  for (int b = 0; b < nband; ++b) {
+    double d[3];
+    if (pair_d<DIM>(P, xi, S.x, int(band[b] & kIdxMask), d) < P.cut2) append(band[b]);
   }
   if (over) {
     atomicOr(S.err, kErrCapacity);

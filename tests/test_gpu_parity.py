@@ -78,6 +78,29 @@ def test_neighbors_ragged_tiles_and_tiny_case(sisph):
         sim.close()
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_neighbors_of_particles_outside_the_box(sisph, dim):
+    # fluid that left a non-periodic box is clamped into the edge cells; its
+    # neighbours must still match the definition exactly
+    case = workloads.dam_break_2d(dx=0.05) if dim == 2 else workloads.dam_break_3d(dx=0.06)
+    case = dict(case)
+    rng = np.random.Generator(np.random.PCG64(3))
+    fl = np.nonzero(case["kind"] == 0)[0]
+    pick = rng.choice(fl, 12, replace=False)
+    for key, k in (("x", 0), ("y", 1), ("z", 2))[:dim]:
+        a = case[key].copy()
+        span = case["hi"][k] - case["lo"][k]
+        a[pick[:4]] = case["hi"][k] + rng.uniform(0.0, 0.3 * span, 4)
+        a[pick[4:8]] = case["lo"][k] - rng.uniform(0.0, 0.3 * span, 4)
+        a[pick[8:]] = case["hi"][k] + 0.05 * rng.uniform(0, 1, 4)   # close together, outside
+        case[key] = a
+    sim = sisph.Simulation(case, precision=sisph.MIXED)
+    cg, ig = sim.neighbors()
+    co, io = oracle.neighbors(case)
+    assert np.array_equal(cg, co) and np.array_equal(ig, io)
+    sim.close()
+
+
 @pytest.mark.parametrize("name", ["tgv_perturbed", "ldc", "db2d", "db3d"])
 def test_density_and_normals_fp64(sisph, name):
     case = CASES[name]
