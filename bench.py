@@ -138,6 +138,22 @@ def sweep_bytes(counts_fluid, n_walls_rows, wall_counts, prec_bytes):
     return float(fluid), float(walls)
 
 
+def aggregate_time(t_ms, world, device=None):
+    """Slowest rank's timed-region length (ms): every rank's replica must finish
+    before the job has processed all of its particle-steps."""
+    if world <= 1:
+        return float(t_ms)
+    import torch
+    t = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n_particles, steps, t_ms, world):
+    """Whole-job throughput: all ranks' particle-steps over the slowest time."""
+    return world * n_particles * steps / (t_ms * 1e-3)
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_1908_01762_gb300 import sisph
@@ -187,10 +203,7 @@ def run_ours(args, rank, world):
     it1 = np.array([s.total_iters for s in sim.stats()])
     nsw, sweep_ms, _ = sisph.sisph_profile_get(sim.h, "ppe_sweeps")
     sisph.sisph_profile_enable(sim.h, False)
-    if world > 1:
-        t = torch.tensor([t_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(t.item())
+    t_ms = aggregate_time(t_ms, world, dev)
 
     # algorithmic bytes of the sweep kernel (neighbour lists at the last r*)
     counts, idx = sisph.sisph_neighbors(sim.h, n)
@@ -221,7 +234,7 @@ def run_ours(args, rank, world):
     peak, peak_kind = measured_hbm_peak()
     interactions = pairs
 
-    value = world * n * args.steps / (t_ms * 1e-3)
+    value = job_value(n, args.steps, t_ms, world)
     out = {
         "metric": "particle-steps/s (one SISPH time step of Algorithm 1 per particle)",
         "value": value,

@@ -307,28 +307,37 @@ __global__ void __launch_bounds__(256) k_build(State S) {
         for (int kind = 0; kind < 2; ++kind) {
           if (kind == 1 && P.nw == 0) break;
           long long q = P.key_base + (long long)kind * P.slots + m;
-          unsigned beg = S.hist[q], end = S.hist[q + 1];
-          for (unsigned j = beg; j < end; ++j) {
-            if (exact_all) {
+          const unsigned beg = S.hist[q], end = S.hist[q + 1];
+          if (exact_all) {
+            for (unsigned j = beg; j < end; ++j) {
               double d[3];
               if (pair_d<DIM>(P, xi, S.x, int(j), d) < P.cut2) append(j | code);
-              continue;
             }
-            float4 pj = S.pf4[j];
-            float dx = fx - pj.x, dy = fy - pj.y;
-            float r2f = dx * dx + dy * dy;
-            if (DIM == 3) {
-              float dz = fz - pj.z;
-              r2f += dz * dz;
-            }
-            if (r2f < lo_band) {
-              append(j | code);
-            } else if (r2f <= hi_band) {
-              if (nband < kBand) {
-                band[nband++] = j | code;
-              } else {
-                double d[3];
-                if (pair_d<DIM>(P, xi, S.x, int(j), d) < P.cut2) append(j | code);
+            continue;
+          }
+          // candidates 8 at a time: the loads go out together; slots past the
+          // cell's end get a far-away position and are rejected by the test
+          for (unsigned j0 = beg; j0 < end; j0 += 8) {
+            float4 pj[8];
+            _Pragma("unroll") for (int u = 0; u < 8; ++u)
+              pj[u] = j0 + u < end ? S.pf4[j0 + u] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
+            _Pragma("unroll") for (int u = 0; u < 8; ++u) {
+              const unsigned j = j0 + u;
+              float dx = fx - pj[u].x, dy = fy - pj[u].y;
+              float r2f = dx * dx + dy * dy;
+              if (DIM == 3) {
+                float dz = fz - pj[u].z;
+                r2f += dz * dz;
+              }
+              if (r2f < lo_band) {
+                append(j | code);
+              } else if (r2f <= hi_band) {
+                if (nband < kBand) {
+                  band[nband++] = j | code;
+                } else {
+                  double d[3];
+                  if (pair_d<DIM>(P, xi, S.x, int(j), d) < P.cut2) append(j | code);
+                }
               }
             }
           }

@@ -90,11 +90,12 @@ __global__ void k_density(State S) {
   Geo<DIM, MX> G;
   G.init(S, i);
   R acc = R(0);
-  ROW_LOOP(S, i, {
+  ROW_CHUNKS(S, i, {
     int j;
     R d[3];
     R r2 = G.pair(S, P, K.lc, e, j, d);
-    acc += mass<MX>(S, j) * poly_w<R>(qof<R>(sqrt_r(r2), K.h, K.ih));
+    R w = mass<MX>(S, j) * poly_w<R>(qof<R>(sqrt_r(r2), K.h, K.ih));
+    acc += valid ? w : R(0);
   })
   acc *= K.sig;
   S.rho[i] = double(acc);
@@ -233,11 +234,11 @@ __global__ void k_stage1(State S) {
   R dti[3];
   _Pragma("unroll") for (int k = 0; k < 3; ++k) dti[k] = uti[k] - ui[k];
   R f[3] = {R(0), R(0), R(0)};
-  ROW_LOOP(S, i, {
+  ROW_CHUNKS(S, i, {
     int j;
     R d[3];
     R r2 = G.pair(S, P, K.lc, e, j, d);
-    if (j != i) {
+    if (valid && j != i) {
       R r = sqrt_r(r2);
       R dw = K.dsc * poly_dw<R>(qof<R>(r, K.h, K.ih));
       R fr = r > R(0) ? divr(dw, r) : R(0);
@@ -458,9 +459,9 @@ __global__ void k_pgrad_gtvf1(State S) {
   const float iri = 1.f / ri;
   const bool symm = P.pgrad_symm != 0;
   float f[3] = {0.f, 0.f, 0.f}, acc[3] = {0.f, 0.f, 0.f};
-  ROW_LOOP(S, i, {
+  ROW_CHUNKS(S, i, {
     const int j = int(e & kIdxMask);
-    if (j != i) {
+    if (valid && j != i) {
       float4 pj4 = S.pf4[j];
       float d[3];
       float r2 = pair_f<DIM>(K.lc, pi4, pj4, e >> kCodeShift, d);

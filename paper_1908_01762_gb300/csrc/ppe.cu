@@ -54,11 +54,9 @@ __global__ void k_setup_fluid(State S) {
     const R idt = R(1.0 / P.dt);
     const R four_iri = R(4) / ri;
     R rhs = R(0), rc = R(0), dg = R(0), dc = R(0);
-    const int cnt = S.ncnt[i];
-    const long long n = S.n;
     R *coef = static_cast<R *>(S.coef);
-    _Pragma("unroll 4") for (int k = 0; k < cnt; ++k) {
-      unsigned e = S.nbr[(long long)k * n + i];
+    ROW_CHUNKS(S, i, {
+      const int k = _q0 + _u;
       int j = int(e & kIdxMask);
       R fac = R(0);
       if (j != i) {
@@ -83,6 +81,7 @@ __global__ void k_setup_fluid(State S) {
         _Pragma("unroll") for (int q = 0; q < DIM; ++q) ud += (ui[q] - uj[q]) * d[q];
         R src = -divr(mj * idt * fr * ud, rj);
         fac = divr(four_iri * mj * (fr * r2), (ri + rj) * (r2 + eh2));
+        if (!valid) { src = R(0); fac = R(0); }
         if constexpr (MX) {
           kahan_add(rhs, rc, src);
           kahan_add(dg, dc, fac);
@@ -91,8 +90,8 @@ __global__ void k_setup_fluid(State S) {
           dg += fac;
         }
       }
-      coef[(long long)k * n + i] = fac;
-    }
+      if (valid) coef[(long long)k * _n + i] = fac;
+    })
     bool fs = P.free_surface && (double(ri) / P.rho0 < S.fs_ratio);
     bool active = (dg != R(0)) && !fs;
     static_cast<R *>(S.prhs)[i] = active ? rhs : R(0);

@@ -240,6 +240,29 @@ __device__ __forceinline__ R divr(R a, R b) {
   else return a / b;
 }
 
+// Rows in chunks of 8 slots: the 8 entries are loaded first and every slot
+// past the row's end is padded with the particle itself, so the gathers of a
+// chunk do not depend on branches and can all be in flight at once; `valid`
+// masks the padded slots out of the sums.
+#define ROW_CHUNKS(S, i, ...)                                                      \
+  {                                                                                \
+    const int _cnt = S.ncnt[i];                                                    \
+    const long long _n = S.n;                                                      \
+    const unsigned _self = unsigned(i) | (stencil_code(0, 0, 0) << kCodeShift);    \
+    for (int _q0 = 0; _q0 < _cnt; _q0 += 8) {                                      \
+      unsigned _e[8];                                                              \
+      _Pragma("unroll") for (int _u = 0; _u < 8; ++_u) {                          \
+        const int _q = _q0 + _u;                                                   \
+        _e[_u] = _q < _cnt ? S.nbr[(long long)_q * _n + i] : _self;               \
+      }                                                                            \
+      _Pragma("unroll") for (int _u = 0; _u < 8; ++_u) {                          \
+        const unsigned e = _e[_u];                                                 \
+        const bool valid = _q0 + _u < _cnt;                                        \
+        __VA_ARGS__                                                                \
+      }                                                                            \
+    }                                                                              \
+  }
+
 __device__ __forceinline__ void store_r(void *base, long long i, double v, int mixed) {
   if (mixed) static_cast<float *>(base)[i] = float(v);
   else static_cast<double *>(base)[i] = v;
