@@ -61,6 +61,30 @@ def make_workload(name):
     raise SystemExit(f"unknown workload {name}")
 
 
+TRAFFIC_PROFILES = {"c2": "profiles/ppe_sweeps_tgv400_traffic.md",
+                    "c4": "profiles/ppe_sweeps_dambreak3d.md"}
+
+
+def measured_traffic(workload):
+    """DRAM bytes per launch of the sweep kernel from the committed ncu summary,
+    or None if there is none for this workload or the kernel source changed
+    since the counters were taken."""
+    import hashlib
+    path = TRAFFIC_PROFILES.get(workload)
+    if not path or not os.path.exists(os.path.join(ROOT, path)):
+        return None
+    vals = {}
+    for line in open(os.path.join(ROOT, path)):
+        if ":" in line and line.split(":")[0].strip() in ("traffic_per_launch_bytes", "kernel_source_sha1"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    src = os.path.join(ROOT, "paper_1908_01762_gb300", "csrc", "ppe.cu")
+    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    if vals.get("kernel_source_sha1") != sha or "traffic_per_launch_bytes" not in vals:
+        return None
+    return float(vals["traffic_per_launch_bytes"])
+
+
 def measured_hbm_peak():
     try:
         with open(MEASURED_PEAKS) as f:
@@ -256,7 +280,7 @@ def run_ours(args, rank, world):
         "roofline": {"kernel": "ppe_sweeps (persistent damped-Jacobi solve)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
-                     "traffic": None, "peak_source": peak_kind,
+                     "traffic": measured_traffic(args.workload), "peak_source": peak_kind,
                      "bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms,
                      "launches": nsw,
                      "share_of_step": (sweep_ms / t_ms) if t_ms else None},
