@@ -268,7 +268,7 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double *sh) {
 // read with ld.global.cg.
 // ---------------------------------------------------------------------------
 template <bool MX>
-__global__ void __launch_bounds__(256) k_sweeps(State S) {
+__global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
   using R = typename std::conditional<MX, float, double>::type;
   __shared__ double sh[64];
   __shared__ int flag;
@@ -302,10 +302,19 @@ __global__ void __launch_bounds__(256) k_sweeps(State S) {
         int c = S.case_of[w];
         if (k > 0 && __ldcg(done + c) && __ldcg(fin + c) != k) continue;
         R acc = wh[r];
-        int cnt = S.wcnt[r];
-        for (int q = 0; q < cnt; ++q) {
-          long long o = (long long)q * nwl + r;
-          acc += wc[o] * pc[S.widx[o]];
+        const int cnt = S.wcnt[r];
+        for (int q0 = 0; q0 < cnt; q0 += 8) {
+          int jj[8];
+          R ww[8];
+          _Pragma("unroll") for (int u = 0; u < 8; ++u) {
+            const int q = q0 + u;
+            const long long o = (long long)q * nwl + r;
+            jj[u] = q < cnt ? S.widx[o] : w;
+            ww[u] = q < cnt ? wc[o] : R(0);
+          }
+          R pv[8];
+          _Pragma("unroll") for (int u = 0; u < 8; ++u) pv[u] = pc[jj[u]];
+          _Pragma("unroll") for (int u = 0; u < 8; ++u) acc += ww[u] * pv[u];
         }
         R pw = acc * wsinv[r];
         if (S.cases[c].free_surface && pw < R(0)) pw = R(0);

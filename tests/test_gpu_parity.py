@@ -304,3 +304,18 @@ def test_checkpoint_resumes_bit_identically(sisph, tmp_path):
         assert np.array_equal(a.get(f), b.get(f)), f
     a.close()
     b.close()
+
+
+def test_eisph_single_sweep_matches_oracle(sisph):
+    # EISPH (Sec. 4.2): the same PPE with a single Jacobi iteration per step
+    case = with_params(workloads.taylor_green(40, perturb=0.05), max_iter=1)
+    sim = sisph.Simulation(case, min_iter=1)
+    ref = oracle.Sim(case, min_iter=1)
+    for _ in range(3):
+        rc = sim.step(1)
+        ref.step(1)
+        st = sim.stats()[0]
+        assert st.iters == 1
+    for f in ("x", "y", "u", "v", "p"):
+        assert relerr(sim.get(f), ref.get(f)) < FP64_TOL, f
+    sim.close()
