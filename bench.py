@@ -61,24 +61,30 @@ def make_workload(name):
     raise SystemExit(f"unknown workload {name}")
 
 
-TRAFFIC_PROFILES = {"c2": "profiles/ppe_sweeps_tgv400_traffic.md",
-                    "c4": "profiles/ppe_sweeps_dambreak3d.md"}
+# Profiled sites (one kernel each, except the 9-kernel cell sort) and the
+# source file of each, for matching a committed ncu traffic summary.
+SITES = {"check": "nbr.cu", "sort": "nbr.cu", "build": "nbr.cu", "sync": "nbr.cu",
+         "filter": "nbr.cu", "density": "passes.cu", "ghost": "passes.cu",
+         "stage1": "passes.cu", "stage1_walls": "passes.cu", "ppe_setup": "ppe.cu",
+         "ppe_setup_wall": "ppe.cu", "ppe_sweeps": "ppe.cu", "pref": "passes.cu",
+         "pgrad_gtvf": "passes.cu", "pgrad": "passes.cu", "gtvf": "passes.cu",
+         "update": "passes.cu"}
 
 
-def measured_traffic(workload):
-    """DRAM bytes per launch of the sweep kernel from the committed ncu summary,
-    or None if there is none for this workload or the kernel source changed
-    since the counters were taken."""
+def measured_traffic(workload, site):
+    """DRAM bytes per launch of one kernel from the committed ncu summary
+    profiles/<site>_<workload>_traffic.md, or None if there is none or the
+    kernel's source file changed since the counters were taken."""
     import hashlib
-    path = TRAFFIC_PROFILES.get(workload)
-    if not path or not os.path.exists(os.path.join(ROOT, path)):
+    path = os.path.join(ROOT, "profiles", f"{site}_{workload}_traffic.md")
+    if not os.path.exists(path):
         return None
     vals = {}
-    for line in open(os.path.join(ROOT, path)):
+    for line in open(path):
         if ":" in line and line.split(":")[0].strip() in ("traffic_per_launch_bytes", "kernel_source_sha1"):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    src = os.path.join(ROOT, "paper_1908_01762_gb300", "csrc", "ppe.cu")
+    src = os.path.join(ROOT, "paper_1908_01762_gb300", "csrc", SITES[site])
     sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
     if vals.get("kernel_source_sha1") != sha or "traffic_per_launch_bytes" not in vals:
         return None
@@ -110,7 +116,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -162,6 +168,48 @@ def sweep_bytes(counts_fluid, n_walls_rows, wall_counts, prec_bytes):
     return float(fluid), float(walls)
 
 
+def kernel_bytes(site, mixed, dim, n_f, n, s_f, s_all, ss_all):
+    """Algorithmic bytes of one launch of a neighbour-pass kernel: every
+    particle's own streams read and written once, and per neighbour slot the
+    4-byte entry (plus a stored coefficient where the kernel writes one).
+    Neighbours' data are gathers that the Morton order keeps in cache, so
+    they are not counted (the same convention as the sweep model).
+    n_f fluid and n particles, s_f slots in fluid rows, s_all slots in all
+    rows, ss_all skin-list slots in all rows; dim-component FP64 vectors take
+    8 * dim bytes.  None: no model for this site."""
+    D = dim
+    if mixed:
+        per = {"density": (n_f * (16 + 4 + 8 + 4), 4 * s_f),
+               "stage1": (n_f * (16 + 16 + 16 + 4 + 40 * D), 4 * s_f),
+               "ppe_setup": (n_f * 68, 8 * s_f),
+               "pgrad_gtvf": (n_f * (52 + 56 * D), 4 * s_f)}
+    else:
+        per = {"density": (n_f * (8 * D + 12), 4 * s_f),
+               "stage1": (n_f * (12 + 40 * D), 4 * s_f),
+               "ppe_setup": (n_f * (16 * D + 60), 12 * s_f),
+               "pgrad": (n_f * (24 * D + 20), 4 * s_f)}
+    per["filter"] = (n * 32, 4 * ss_all + 4 * s_all)
+    if site not in per:
+        return None
+    a, b = per[site]
+    return float(a + b)
+
+
+def site_times(sisph, sim, steps):
+    """Device time per step of every profiled site, one site at a time, timed
+    by event nodes inside the replayed step graph (outside the timed region)."""
+    out = {}
+    for site in SITES:
+        sisph.sisph_profile_enable(sim.h, True, site)
+        for _ in range(steps):
+            sim.step(1)
+        nl, ms, _ = sisph.sisph_profile_get(sim.h, site)
+        if nl:
+            out[site] = {"launches_per_step": nl / steps, "ms_per_step": ms / steps}
+    sisph.sisph_profile_enable(sim.h, False)
+    return out
+
+
 def aggregate_time(t_ms, world, device=None):
     """Slowest rank's timed-region length (ms): every rank's replica must finish
     before the job has processed all of its particle-steps."""
@@ -204,13 +252,23 @@ def run_ours(args, rank, world):
         sim.step(1)
     torch.cuda.synchronize()
 
-    # time the dominant kernel live, inside the graph-replayed steps
-    sisph.sisph_profile_enable(sim.h, True, "ppe_sweeps")
+    # per-site device time per step (outside the timed region), then the
+    # dominant kernel with a byte model is timed live inside the timed steps
+    mixed = prec == sisph.MIXED
+    dim = cases[0]["dim"]
+    if args.roofline_kernel:
+        sites = {}
+        roof_site = args.roofline_kernel
+    else:
+        sites = site_times(sisph, sim, 3)
+        modeled = [k for k in sites if k == "ppe_sweeps" or kernel_bytes(k, mixed, dim, 1, 1, 1, 1, 1)]
+        roof_site = max(modeled, key=lambda k: sites[k]["ms_per_step"])
+    sisph.sisph_profile_enable(sim.h, True, roof_site)
     launches0 = sisph.sisph_launch_count(sim.h)
     it0 = np.array([s.total_iters for s in sim.stats()])
+    rb0 = np.array([s.rebuilds for s in sim.stats()])
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    counts_hist = []
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -225,17 +283,17 @@ def run_ours(args, rank, world):
     t_ms = float(np.sum(ms_steps))
     launches = sisph.sisph_launch_count(sim.h) - launches0
     it1 = np.array([s.total_iters for s in sim.stats()])
-    nsw, sweep_ms, _ = sisph.sisph_profile_get(sim.h, "ppe_sweeps")
+    nk, kern_ms, _ = sisph.sisph_profile_get(sim.h, roof_site)
     sisph.sisph_profile_enable(sim.h, False)
     t_ms = aggregate_time(t_ms, world, dev)
 
-    # algorithmic bytes of the sweep kernel (neighbour lists at the last r*)
+    # algorithmic bytes (neighbour lists at the last r*)
     counts, idx = sisph.sisph_neighbors(sim.h, n)
     starts = np.concatenate([[0], np.cumsum(counts)])
     fl = kinds == 0
-    rb = 4 if prec == sisph.MIXED else 8
+    rb = 4 if mixed else 8
     offs = np.cumsum([0] + [c["n"] for c in cases])
-    total_bytes = 0.0
+    sweep_total = 0.0
     pairs = 0.0
     for ci in range(len(cases)):
         sl = slice(offs[ci], offs[ci + 1])
@@ -246,17 +304,21 @@ def run_ours(args, rank, world):
             if walls.size else np.zeros(0)
         fb, wb = sweep_bytes(cnt_c[flc], walls.size, wall_counts, rb)
         its = float(it1[ci] - it0[ci])
-        total_bytes += its * fb + (its + args.steps) * wb
+        sweep_total += its * fb + (its + args.steps) * wb
         pairs += its * float(np.sum(cnt_c[flc]))
-    publish = n * (rb + 8 + (rb if prec == sisph.MIXED else 0))
-    total_bytes += args.steps * publish
+    sweep_total += args.steps * n * (rb + 8 + (rb if mixed else 0))     # publish p
     sweeps = float(np.sum(it1 - it0))
     iters_per_step = sweeps / args.steps / len(cases)
-    per_launch_bytes = total_bytes / nsw if nsw else 0.0
-    avg_ms = sweep_ms / nsw if nsw else float("nan")
-    achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9 if nsw else None
+    if roof_site == "ppe_sweeps":
+        per_launch_bytes = sweep_total / nk if nk else 0.0
+    else:
+        nskin = sim.get("nskin")
+        per_launch_bytes = kernel_bytes(roof_site, mixed, dim, n_fluid, n, float(np.sum(counts[fl])),
+                                        float(np.sum(counts)), float(np.sum(nskin)))
+    avg_ms = kern_ms / nk if nk else float("nan")
+    achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9 if nk else None
     peak, peak_kind = measured_hbm_peak()
-    interactions = pairs
+    rebuilds = np.array([s.rebuilds for s in sim.stats()]) - rb0
 
     value = job_value(n, args.steps, t_ms, world)
     out = {
@@ -270,20 +332,23 @@ def run_ours(args, rank, world):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if prec == sisph.MIXED else "f64",
+        "dtype": "f32" if mixed else "f64",
         "data": "synthetic",
         "config": {"workload": desc, "n_particles": n, "n_fluid": n_fluid,
                    "cases": len(cases), "precision": args.precision,
                    "ppe_sweeps_per_step": iters_per_step, "l2": "flushed between steps (256 MiB write)",
-                   "graph": "CUDA graph replay per step", "parallelism": f"replicas{world}"},
-        "ppe_interactions_per_s": world * interactions / (t_ms * 1e-3),
-        "roofline": {"kernel": "ppe_sweeps (persistent damped-Jacobi solve)", "bound": "hbm",
+                   "graph": "CUDA graph replay per step", "parallelism": f"replicas{world}",
+                   "neighbour_rebuilds_per_refresh": float(np.mean(rebuilds)) / (2 * args.steps)},
+        "ppe_interactions_per_s": world * pairs / (t_ms * 1e-3),
+        "roofline": {"kernel": roof_site, "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
-                     "traffic": measured_traffic(args.workload), "peak_source": peak_kind,
+                     "traffic": measured_traffic(args.workload, roof_site), "peak_source": peak_kind,
                      "bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms,
-                     "launches": nsw,
-                     "share_of_step": (sweep_ms / t_ms) if t_ms else None},
+                     "launches": nk,
+                     "share_of_step": (kern_ms / t_ms) if t_ms else None},
+        "sites_ms_per_step": {k: round(v["ms_per_step"], 5) for k, v in
+                              sorted(sites.items(), key=lambda kv: -kv[1]["ms_per_step"])},
         "clocks": clk.summary(),
         "gpu_launches": int(launches * world),
     }
@@ -429,7 +494,7 @@ def study_tolerance(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2")
@@ -437,6 +502,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--roofline-kernel", default=None, choices=sorted(SITES),
+                    help="time this site live instead of the dominant one (skips the site table)")
     ap.add_argument("--study", choices=["tolerance"], default=None,
                     help="run a parameter study instead of the benchmark")
     args = ap.parse_args()

@@ -105,6 +105,11 @@ typedef struct {
   double fs_ratio;              /* 0.8 */
   int32_t residual_form;        /* 0: max(Lambda, sum|p|); 1: max(N_F Lambda, sum|p|) */
   int32_t nbr_capacity;         /* neighbours per particle; 0 = from dim and h */
+  double skin;                  /* Verlet skin s as a fraction of 3h (0.15): the
+                                   lists are rebuilt from a cell sort only when a
+                                   fluid particle of the case moved more than s/2
+                                   since the last rebuild, and filtered exactly to
+                                   N(i) at every refresh; 0 rebuilds every time */
   int32_t block;                /* threads per block / tile size (64..1024, mult. of 32) */
   int32_t use_graph;            /* capture sisph_step in a CUDA graph and replay it */
   double barrier_timeout_ms;    /* budget of one grid-barrier wait */
@@ -121,6 +126,7 @@ typedef struct {
   double p_ref;                 /* background pressure in use */
   int64_t total_iters;          /* sweeps summed over every solve so far */
   int64_t solves;               /* PPE solves so far */
+  int64_t rebuilds;             /* cell sorts + skin-list rebuilds so far */
 } sisph_case_stats;
 
 /* Field identifiers for sisph_get / sisph_set. */
@@ -144,7 +150,8 @@ typedef struct {
 #define SISPH_F_DX 17    /* GTVF displacement r^K - r^0 of the last step */
 #define SISPH_F_DY 18
 #define SISPH_F_DZ 19
-#define SISPH_F_COUNT 20
+#define SISPH_F_NSKIN 20 /* length of the particle's skin list (read-only) */
+#define SISPH_F_COUNT 21
 
 /* Fill defaults: FP64, omega 0.5, min_iter 2, eta 0.01, fs_ratio 0.8, ... */
 void sisph_default_options(sisph_options *opt);
@@ -167,8 +174,12 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *particles,
 
 void sisph_destroy(sisph_t s);
 
-/* Sort into Morton-ordered cells and rebuild the neighbour lists at the
- * current positions (N(i) = {j : |r_ij|^2 < (3h)^2}, minimum image). */
+/* Bring the neighbour lists to the current positions: N(i) = {j : |r_ij|^2 <
+ * (3h)^2}, minimum image, exactly.  A case whose fluid moved more than s/2
+ * since its last rebuild (every case, after sisph_set of a position) is first
+ * sorted into Morton-ordered cells and gets new skin lists; then every list is
+ * filtered from its skin list.  sisph_step does this twice per step; call it
+ * after sisph_set of a position before using the lists outside a step. */
 int sisph_build_neighbors(sisph_t s);
 
 /* Neighbour lists in the caller's order: counts[n] and, if idx is not NULL,

@@ -49,6 +49,7 @@ struct sisph_s {
   State S{};
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;     // captures the body of the rebuild node
   sisph_options opt{};
   std::vector<sisph_case_params> prm;
   std::vector<CaseDev> hc;
@@ -58,16 +59,16 @@ struct sisph_s {
   int64_t n = 0, nf = 0, nw = 0;
   int kmax = 1;
   int grid = 1;
-  int parity = 0;
-  // graphs, one per buffer parity
-  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  // the captured step
+  cudaGraphExec_t gexec = nullptr;
   bool graph_failed = false;
+  bool no_conditional = false;     // capture the rebuild group unconditionally
   int graph_kernels = 0;
   // profiling
   bool profiling = false;
   std::string prof_only;           // empty: every kernel, no graphs
   bool capturing = false;
-  std::vector<Pending> gsites[2];  // event nodes inside the captured graphs
+  std::vector<Pending> gsites;     // event nodes inside the captured graph
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
   std::map<std::string, ProfRec> prof;
@@ -118,7 +119,7 @@ void before_cb(void *ctx, const char *name) {
     cudaEventCreate(&p.a);
     cudaEventCreate(&p.b);
     cudaEventRecordWithFlags(p.a, s->stream, cudaEventRecordExternal);
-    s->gsites[s->parity].push_back(p);
+    s->gsites.push_back(p);
     return;
   }
   Pending p;
@@ -145,7 +146,7 @@ void after_cb(void *ctx, const char *name, double units, int nk) {
   if (s->counting) s->launches += nk;
   if (!profiled(s, name)) return;
   if (s->capturing) {
-    Pending &p = s->gsites[s->parity].back();
+    Pending &p = s->gsites.back();
     p.units = units;
     p.nk = nk;
     cudaEventRecordWithFlags(p.b, s->stream, cudaEventRecordExternal);
@@ -185,10 +186,10 @@ void drain_profile(sisph_t s) {
 }
 
 // After one replay of the captured step: read its event nodes.
-void drain_graph_sites(sisph_t s, int par) {
-  if (s->gsites[par].empty()) return;
+void drain_graph_sites(sisph_t s) {
+  if (s->gsites.empty()) return;
   cudaStreamSynchronize(s->stream);
-  for (auto &p : s->gsites[par]) {
+  for (auto &p : s->gsites) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, p.a, p.b);
     ProfRec &r = s->prof[p.name];
@@ -198,33 +199,81 @@ void drain_graph_sites(sisph_t s, int par) {
   }
 }
 
-void swap_buffers(sisph_t s) {
-  State &S = s->S;
-  for (int k = 0; k < 3; ++k) {
-    std::swap(S.x[k], S.bx[k]);
-    std::swap(S.xn[k], S.bxn[k]);
-    std::swap(S.u[k], S.bu[k]);
-    std::swap(S.ut[k], S.but[k]);
-  }
-  std::swap(S.m, S.bm);
-  std::swap(S.rho, S.brho);
-  std::swap(S.p, S.bp);
-  std::swap(S.uid, S.buid);
-  s->parity ^= 1;
+// Capture the rebuild group into the body of a conditional node of the step
+// graph: the node runs its body only when the check marked some case.  Body
+// kernels are counted on the device (k_zero_hist), not here.
+cudaError_t capture_rebuild_conditional(sisph_t s, int mode, bool first) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s->stream, &st, nullptr, &g, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  cudaGraphConditionalHandle h;
+  e = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
+  if (e != cudaSuccess) return e;
+  e = launch_set_conditional(s->S, mk_launch(s), h);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamGetCaptureInfo(s->stream, &st, nullptr, &g, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  // (the struct holds a union without a default constructor: zeroed storage)
+  alignas(cudaGraphNodeParams) unsigned char cp_mem[sizeof(cudaGraphNodeParams)];
+  memset(cp_mem, 0, sizeof(cp_mem));
+  cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(cp_mem);
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeIf;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  e = cudaStreamUpdateCaptureDependencies(s->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamBeginCaptureToGraph(s->side, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  Launch B = mk_launch(s);
+  B.stream = s->side;
+  B.before = nullptr;
+  B.after = nullptr;
+  cudaError_t eb = launch_refresh_rebuild(s->S, B, mode, first, true);
+  cudaGraph_t out = nullptr;
+  e = cudaStreamEndCapture(s->side, &out);
+  return eb != cudaSuccess ? eb : e;
 }
 
-cudaError_t do_build(sisph_t s, int mode, bool first) {
+// One refresh of the neighbour lists (mode 0 at x, mode 1 at r*).  The
+// buffers never change places on the host, so one captured graph serves
+// every step.  Whether the cell sort and skin lists are rebuilt is decided on
+// the device: in a captured step by a conditional node (unless a profiled
+// site lies in the group, whose kernels then return at once without a
+// rebuild), in direct launches by reading the decision back.
+cudaError_t do_refresh(sisph_t s, int mode, bool first) {
   Launch L = mk_launch(s);
-  const double *pos[3];
-  for (int k = 0; k < 3; ++k) pos[k] = mode == 0 ? s->S.x[k] : s->S.xs[k];
-  cudaError_t e = launch_sort(s->S, L, pos, mode, first);
+  cudaError_t e = launch_refresh_check(s->S, L, mode);
   if (e != cudaSuccess) return e;
-  swap_buffers(s);
-  if (first) {
-    e = launch_copy_static(s->S, L);
-    if (e != cudaSuccess) return e;
+  const bool prof_group =
+      s->profiling && (s->prof_only.empty() || s->prof_only == "sort" || s->prof_only == "build");
+  if (s->capturing && !prof_group && !s->no_conditional) {
+    e = capture_rebuild_conditional(s, mode, first);
+  } else if (s->capturing) {
+    e = launch_refresh_rebuild(s->S, L, mode, first, false);
+  } else {
+    int any = 0;
+    e = cudaMemcpyAsync(&any, s->S.anyneed, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess && any) e = launch_refresh_rebuild(s->S, L, mode, first, false);
   }
-  return launch_build(s->S, L);
+  if (e == cudaSuccess) e = launch_refresh_finish(s->S, L, mode);
+  return e;
+}
+
+// Next refresh rebuilds every case: mode 1 at the current positions, mode 2
+// at the stored rebuild positions (the int is written as 0 then its low byte).
+cudaError_t force_rebuild(sisph_t s, int mode = 1) {
+  cudaError_t e = cudaMemsetAsync(s->S.force, 0, sizeof(int), s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->S.force, mode, 1, s->stream);
+  return e;
 }
 
 cudaError_t do_ppe(sisph_t s) {
@@ -237,11 +286,11 @@ cudaError_t do_ppe(sisph_t s) {
 
 cudaError_t do_step(sisph_t s) {
   Launch L = mk_launch(s);
-  cudaError_t e = do_build(s, 0, false);              // neighbours at r^n
+  cudaError_t e = do_refresh(s, 0, false);            // neighbours at r^n
   if (e == cudaSuccess) e = launch_density(s->S, L);  // rho (Eq. summation_density)
   if (e == cudaSuccess) e = launch_ghost(s->S, L, 0); // no-slip ghost velocity
   if (e == cudaSuccess) e = launch_stage1(s->S, L);   // u*, r* (Eqs. int:vint, int:rnp1)
-  if (e == cudaSuccess) e = do_build(s, 1, false);    // neighbours at r*
+  if (e == cudaSuccess) e = do_refresh(s, 1, false);  // neighbours at r*
   if (e == cudaSuccess) e = do_ppe(s);                // Eqs. sph-ppe, p-sor, convergence
   if (e == cudaSuccess) e = launch_pref(s->S, L);     // p_ref after the first solve
   if (s->S.mixed) {
@@ -280,17 +329,15 @@ int check_status(sisph_t s, bool sweeps_ran) {
 bool valid_handle(sisph_t s) { return s != nullptr && s->S.n > 0; }
 
 void destroy_graphs(sisph_t s) {
-  for (int p = 0; p < 2; ++p) {
-    if (s->gexec[p]) {
-      cudaGraphExecDestroy(s->gexec[p]);
-      s->gexec[p] = nullptr;
-    }
-    for (auto &q : s->gsites[p]) {
-      cudaEventDestroy(q.a);
-      cudaEventDestroy(q.b);
-    }
-    s->gsites[p].clear();
+  if (s->gexec) {
+    cudaGraphExecDestroy(s->gexec);
+    s->gexec = nullptr;
   }
+  for (auto &q : s->gsites) {
+    cudaEventDestroy(q.a);
+    cudaEventDestroy(q.b);
+  }
+  s->gsites.clear();
 }
 
 int setup_case(sisph_t s, int c, const sisph_particles &P, const sisph_case_params &q, int64_t fbeg,
@@ -298,7 +345,15 @@ int setup_case(sisph_t s, int c, const sisph_particles &P, const sisph_case_para
   memset(&D, 0, sizeof(D));
   const int dim = P.dim;
   const double cut = 3.0 * q.h;
-  const double lcmin = cut * (1.0 + 1e-9);
+  // Verlet skin; a periodic box too small for three cells of 3h + s falls
+  // back to rebuilding at every refresh (s = 0)
+  double skin = s->opt.skin * cut;
+  for (int k = 0; k < dim; ++k)
+    if (P.periodic[k] && std::floor((P.hi[k] - P.lo[k]) / ((cut + skin) * (1.0 + 1e-9))) < 3.0) skin = 0.0;
+  const double lcmin = (cut + skin) * (1.0 + 1e-9);
+  D.skin = skin;
+  D.cut_s2 = (cut + skin) * (cut + skin);
+  D.skin_half2 = skin > 0.0 ? 0.25 * skin * skin : -1.0;
   int maxnc = 1;
   for (int k = 0; k < 3; ++k) {
     D.lo[k] = P.lo[k];
@@ -319,6 +374,8 @@ int setup_case(sisph_t s, int c, const sisph_particles &P, const sisph_case_para
       if (ncd < 3.0)
         return fail(nullptr, SISPH_EINVAL,
                     "case " + std::to_string(c) + ": periodic length must hold at least 3 cells of 3h");
+      if (ncd > double(kMaxCellsPerAxis))
+        return fail(nullptr, SISPH_EINVAL, "case " + std::to_string(c) + ": too many cells");
       D.nc[k] = int(ncd);
       D.lc[k] = D.L[k] / double(D.nc[k]);
     } else {
@@ -326,7 +383,8 @@ int setup_case(sisph_t s, int c, const sisph_particles &P, const sisph_case_para
       // an edge cell, which only collects particles that left the box
       D.lc[k] = lcmin;
       double ncd = std::ceil(D.L[k] / lcmin);
-      if (ncd > 1e6) return fail(nullptr, SISPH_EINVAL, "case " + std::to_string(c) + ": too many cells");
+      if (ncd > double(kMaxCellsPerAxis - 2))
+        return fail(nullptr, SISPH_EINVAL, "case " + std::to_string(c) + ": too many cells");
       D.nc[k] = std::max(1, int(ncd)) + 2;
       D.lo[k] = P.lo[k] - lcmin;
     }
@@ -413,6 +471,7 @@ void sisph_default_options(sisph_options *o) {
   o->fs_ratio = 0.8;
   o->residual_form = 0;
   o->nbr_capacity = 0;
+  o->skin = 0.15;
   o->block = 256;
   o->use_graph = 1;
   o->barrier_timeout_ms = 2000.0;
@@ -438,6 +497,7 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
     return fail(nullptr, SISPH_EINVAL, "precision must be SISPH_FP64 or SISPH_MIXED");
   if (!(opt.omega > 0.0 && opt.omega <= 1.0)) return fail(nullptr, SISPH_EINVAL, "omega must be in (0, 1]");
   if (opt.min_iter < 1) return fail(nullptr, SISPH_EINVAL, "min_iter must be >= 1");
+  if (!(opt.skin >= 0.0 && opt.skin <= 1.0)) return fail(nullptr, SISPH_EINVAL, "skin must be in [0, 1]");
   const int dim = parts[0].dim;
   if (dim != 2 && dim != 3) return fail(nullptr, SISPH_EINVAL, "dim must be 2 or 3");
   int64_t ntot = 0, nftot = 0;
@@ -496,7 +556,7 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   long long key_base = 0;
   int64_t pos = 0, wrow = 0, off = 0;
   const int T = opt.block;
-  int capmax = 0;
+  int capmax = 0, scapmax = 0;
   for (int c = 0; c < ncases; ++c) {
     const sisph_particles &P = parts[c];
     int64_t nfc = 0;
@@ -534,6 +594,11 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
       cap = std::min(cap, 1024);
     }
     capmax = std::max(capmax, cap);
+    // skin lists: the same headroom over the (3h + s) ball
+    const double grow = std::pow((3.0 * params[c].h + D.skin) / (3.0 * params[c].h), double(dim));
+    int scap = int(std::ceil(double(cap) * grow));
+    scap = (scap + 3) & ~3;
+    scapmax = std::max(scapmax, scap);
     pos += P.n;
     wrow += nwc;
     off += P.n;
@@ -546,6 +611,7 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   S.K = key_base;
   S.cap = capmax;
   S.wcap = capmax;
+  S.scap = scapmax;
   S.nft = int(s->hft.size());
   S.nwt = int(s->hwt.size());
 
@@ -572,6 +638,7 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
     A(&S.x[k], N); A(&S.xn[k], N); A(&S.u[k], N); A(&S.ut[k], N);
     A(&S.bx[k], N); A(&S.bxn[k], N); A(&S.bu[k], N); A(&S.but[k], N);
     A(&S.xs[k], N); A(&S.us[k], N); A(&S.uw[k], N); A(&S.nrm[k], N); A(&S.nstar[k], N);
+    A(&S.xref[k], N); A(&S.bxref[k], N);
     A(&S.vgt[k], N);
     if (!S.mixed) { A(&S.dg[0][k], N); A(&S.dg[1][k], N); }
   }
@@ -584,6 +651,15 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   }
   A(&S.nbr, N * size_t(S.cap));
   A(&S.ncnt, N);
+  A(&S.snbr, N * size_t(S.scap));
+  A(&S.sncnt, N);
+  A(&S.cell, N);
+  A(&S.bcell, N);
+  A(&S.need, ncases);
+  A(&S.anyneed, 1);
+  A(&S.force, 1);
+  A(&S.nreb, size_t(ncases) + 1);
+  A(&S.nbody, 1);
   const size_t rb = S.mixed ? sizeof(float) : sizeof(double);
   auto AR = [&](void **p, size_t cnt) {
     if (e != cudaSuccess) return;
@@ -627,6 +703,7 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   S.wall_at = dwall_at;
 
   e = cudaStreamCreateWithFlags(&s->own_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     sisph_destroy(s);
     return cuda_fail(nullptr, e, "stream");
@@ -716,6 +793,8 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   if (e == cudaSuccess) e = cudaMemcpy(S.pref_set, ps.data(), ncases * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(S.iters_tot, 0, ncases * sizeof(long long));
   if (e == cudaSuccess) e = cudaMemset(S.solves, 0, ncases * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMemset(S.nreb, 0, (ncases + 1) * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMemset(S.nbody, 0, sizeof(long long));
   if (e == cudaSuccess) e = cudaMemset(S.iters, 0, ncases * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(S.resid, 0, ncases * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(S.lam, 0, ncases * sizeof(double));
@@ -744,7 +823,8 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   S.barrier_budget = (long long)(opt.barrier_timeout_ms * double(clk > 0 ? clk : 2000000));
 
   // first sort (places the walls for good), neighbour lists, wall normals
-  e = do_build(s, 0, true);
+  e = force_rebuild(s);
+  if (e == cudaSuccess) e = do_refresh(s, 0, true);
   if (e == cudaSuccess) e = launch_normals(S, mk_launch(s));
   if (e != cudaSuccess) {
     int rc = cuda_fail(nullptr, e, "initial neighbour build");
@@ -787,12 +867,13 @@ void sisph_destroy(sisph_t s) {
   for (auto ev : s->pool) cudaEventDestroy(ev);
   for (void *p : s->allocs) cudaFree(p);
   if (s->own_stream) cudaStreamDestroy(s->own_stream);
+  if (s->side) cudaStreamDestroy(s->side);
   delete s;
 }
 
 int sisph_build_neighbors(sisph_t s) {
   if (!valid_handle(s)) return fail(s, SISPH_EINVAL, "invalid handle");
-  cudaError_t e = do_build(s, 0, false);
+  cudaError_t e = do_refresh(s, 0, false);
   if (e != cudaSuccess) return cuda_fail(s, e, "build_neighbors");
   return check_status(s, false);
 }
@@ -836,11 +917,8 @@ int sisph_step(sisph_t s, int32_t nsteps) {
   bool use_graph = s->opt.use_graph && !(s->profiling && s->prof_only.empty()) && !s->graph_failed;
   cudaError_t e = cudaSuccess;
   for (int st = 0; st < nsteps && e == cudaSuccess; ++st) {
-    if (use_graph && !s->gexec[s->parity]) {
-      // Capture one step.  Capture records without running, so the state is
-      // restored afterwards; a complete step swaps the buffers twice.
-      const int par = s->parity;
-      const State saved = s->S;
+    if (use_graph && !s->gexec) {
+      // Capture one step (recorded, not run).
       const int64_t l0 = s->launches;
       cudaGraph_t g = nullptr;
       cudaError_t ec = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
@@ -851,30 +929,42 @@ int sisph_step(sisph_t s, int32_t nsteps) {
         ec = cudaStreamEndCapture(s->stream, &g);
         if (es != cudaSuccess) ec = es;
       }
-      if (ec == cudaSuccess) ec = cudaGraphInstantiate(&s->gexec[par], g, 0);
+      if (ec == cudaSuccess) ec = cudaGraphInstantiate(&s->gexec, g, 0);
       if (g) cudaGraphDestroy(g);
       s->graph_kernels = int(s->launches - l0);
       s->launches = l0;
-      s->S = saved;
-      s->parity = par;
-      if (ec != cudaSuccess) {
+      if (ec != cudaSuccess && !s->no_conditional) {
+        // no conditional nodes here: capture again with the rebuild group
+        // launched unconditionally (its kernels return at once when idle)
         cudaGetLastError();
-        s->gexec[par] = nullptr;
-        for (auto &q : s->gsites[par]) {
+        s->gexec = nullptr;
+        for (auto &q : s->gsites) {
           cudaEventDestroy(q.a);
           cudaEventDestroy(q.b);
         }
-        s->gsites[par].clear();
+        s->gsites.clear();
+        s->no_conditional = true;
+        s->err = std::string("conditional graph nodes unavailable: ") + cudaGetErrorString(ec);
+        --st;
+        continue;
+      }
+      if (ec != cudaSuccess) {
+        cudaGetLastError();
+        s->gexec = nullptr;
+        for (auto &q : s->gsites) {
+          cudaEventDestroy(q.a);
+          cudaEventDestroy(q.b);
+        }
+        s->gsites.clear();
         s->graph_failed = true;
         use_graph = false;
         s->err = std::string("CUDA graph capture unavailable, using direct launches: ") + cudaGetErrorString(ec);
       }
     }
     if (use_graph) {
-      e = cudaGraphLaunch(s->gexec[s->parity], s->stream);
+      e = cudaGraphLaunch(s->gexec, s->stream);
       s->launches += s->graph_kernels;
-      if (s->profiling) drain_graph_sites(s, s->parity);
-      // the replayed step performs two buffer swaps: host pointers unchanged
+      if (s->profiling) drain_graph_sites(s);
       continue;
     }
     e = do_step(s);
@@ -904,9 +994,11 @@ int sisph_get(sisph_t s, int32_t field, double *out) {
     case SISPH_F_RHS: src = S.rhs_out; break;
     case SISPH_F_DIAG: src = S.diag_out; break;
     case SISPH_F_DX: case SISPH_F_DY: case SISPH_F_DZ: break;
+    case SISPH_F_NSKIN: src = S.sncnt; break;
     default: return fail(s, SISPH_EINVAL, "unknown field");
   }
   if (field >= SISPH_F_DX && field <= SISPH_F_DZ) e = launch_scatter_disp(S, L, field - SISPH_F_DX, s->d_tmp);
+  else if (field == SISPH_F_NSKIN) e = launch_scatter_field(S, L, src, 2, 0, 0, s->d_tmp);
   else e = launch_scatter_field(S, L, src, 0, 0, 0, s->d_tmp);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, s->d_tmp, size_t(s->n) * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -934,6 +1026,8 @@ int sisph_set(sisph_t s, int32_t field, const double *in) {
   cudaError_t e = cudaMemcpyAsync(s->d_tmp, in, size_t(s->n) * sizeof(double), cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) e = launch_gather_field(S, L, s->d_tmp, dst);
   if (e == cudaSuccess) e = launch_refresh_mirrors(S, L);
+  // moved particles: the next refresh sorts and rebuilds every case
+  if (e == cudaSuccess && field <= SISPH_F_Z) e = force_rebuild(s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "set");
   return SISPH_OK;
@@ -977,7 +1071,7 @@ int sisph_stats(sisph_t s, sisph_case_stats *st) {
   int nc = s->ncases;
   std::vector<int> it(nc), ps(nc);
   std::vector<double> rs(nc), lm(nc), pr(nc);
-  std::vector<long long> tot(nc), sv(nc);
+  std::vector<long long> tot(nc), sv(nc), rb(nc);
   cudaError_t e = cudaStreamSynchronize(s->stream);
   const State &S = s->S;
   if (e == cudaSuccess) e = cudaMemcpy(it.data(), S.iters, nc * sizeof(int), cudaMemcpyDeviceToHost);
@@ -987,6 +1081,7 @@ int sisph_stats(sisph_t s, sisph_case_stats *st) {
   if (e == cudaSuccess) e = cudaMemcpy(pr.data(), S.pref, nc * sizeof(double), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(tot.data(), S.iters_tot, nc * sizeof(long long), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(sv.data(), S.solves, nc * sizeof(long long), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(rb.data(), S.nreb, nc * sizeof(long long), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(s, e, "stats");
   for (int c = 0; c < nc; ++c) {
     st[c].iters = it[c];
@@ -996,6 +1091,7 @@ int sisph_stats(sisph_t s, sisph_case_stats *st) {
     st[c].p_ref = pr[c];
     st[c].total_iters = tot[c];
     st[c].solves = sv[c];
+    st[c].rebuilds = rb[c];
   }
   return SISPH_OK;
 }
@@ -1040,16 +1136,51 @@ int sisph_profile_get(sisph_t s, const char *kernel, int64_t *launches, double *
   return SISPH_OK;
 }
 
-int64_t sisph_launch_count(sisph_t s) { return s ? s->launches : 0; }
+int64_t sisph_launch_count(sisph_t s) {
+  if (!valid_handle(s)) return 0;
+  // kernels launched from the host, plus the rebuild groups that ran inside
+  // conditional nodes of replayed step graphs (counted on the device)
+  long long body = 0;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess ||
+      cudaMemcpy(&body, s->S.nbody, sizeof(long long), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    body = 0;
+  }
+  return s->launches + int64_t(kRebuildKernels) * body;
+}
 
 static const int kCkptFields[] = {SISPH_F_X, SISPH_F_Y, SISPH_F_Z, SISPH_F_U, SISPH_F_V, SISPH_F_W,
                                   SISPH_F_UT, SISPH_F_VT, SISPH_F_WT, SISPH_F_P, SISPH_F_RHO};
+
+// A checkpoint holds the state in the caller's order, the background
+// pressures and, so that a resumed run sorts and sums exactly as the saved
+// one would have, the rebuild positions of the skin lists and whether a
+// forced rebuild was pending.
+static int copy_out(sisph_t s, const double *src, double *host) {
+  Launch L = mk_launch(s);
+  L.before = nullptr;
+  L.after = nullptr;
+  cudaError_t e = launch_scatter_field(s->S, L, src, 0, 0, 0, s->d_tmp);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, s->d_tmp, size_t(s->n) * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  return e == cudaSuccess ? SISPH_OK : cuda_fail(s, e, "checkpoint read");
+}
+
+static int copy_in(sisph_t s, const double *host, double *dst) {
+  Launch L = mk_launch(s);
+  L.before = nullptr;
+  L.after = nullptr;
+  cudaError_t e = cudaMemcpyAsync(s->d_tmp, host, size_t(s->n) * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = launch_gather_field(s->S, L, s->d_tmp, dst);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  return e == cudaSuccess ? SISPH_OK : cuda_fail(s, e, "checkpoint write");
+}
 
 int sisph_save(sisph_t s, const char *path) {
   if (!valid_handle(s) || !path) return fail(s, SISPH_EINVAL, "invalid handle or path");
   FILE *f = fopen(path, "wb");
   if (!f) return fail(s, SISPH_EINVAL, std::string("cannot open ") + path);
-  const char magic[8] = {'S', 'I', 'S', 'P', 'H', 'C', 'K', '1'};
+  const char magic[8] = {'S', 'I', 'S', 'P', 'H', 'C', 'K', '2'};
   int64_t hdr[3] = {s->n, s->ncases, s->dim};
   bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1;
   std::vector<double> buf(size_t(s->n));
@@ -1059,12 +1190,21 @@ int sisph_save(sisph_t s, const char *path) {
     if (rc) { fclose(f); return rc; }
     ok = ok && fwrite(buf.data(), sizeof(double), buf.size(), f) == buf.size();
   }
+  for (int k = 0; k < s->dim; ++k) {
+    int rc = copy_out(s, s->S.xref[k], buf.data());
+    if (rc) { fclose(f); return rc; }
+    ok = ok && fwrite(buf.data(), sizeof(double), buf.size(), f) == buf.size();
+  }
   std::vector<double> pr(s->ncases);
   std::vector<int> ps(s->ncases);
+  int force = 0;
   cudaMemcpy(pr.data(), s->S.pref, s->ncases * sizeof(double), cudaMemcpyDeviceToHost);
   cudaMemcpy(ps.data(), s->S.pref_set, s->ncases * sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemcpy(&force, s->S.force, sizeof(int), cudaMemcpyDeviceToHost);
+  int32_t pending = force != 0;
   ok = ok && fwrite(pr.data(), sizeof(double), pr.size(), f) == pr.size();
   ok = ok && fwrite(ps.data(), sizeof(int), ps.size(), f) == ps.size();
+  ok = ok && fwrite(&pending, sizeof(pending), 1, f) == 1;
   fclose(f);
   return ok ? SISPH_OK : fail(s, SISPH_EINVAL, "write failed");
 }
@@ -1076,7 +1216,7 @@ int sisph_load(sisph_t s, const char *path) {
   char magic[8];
   int64_t hdr[3];
   bool ok = fread(magic, 1, 8, f) == 8 && fread(hdr, sizeof(hdr), 1, f) == 1;
-  if (!ok || memcmp(magic, "SISPHCK1", 8) != 0 || hdr[0] != s->n || hdr[1] != s->ncases || hdr[2] != s->dim) {
+  if (!ok || memcmp(magic, "SISPHCK2", 8) != 0 || hdr[0] != s->n || hdr[1] != s->ncases || hdr[2] != s->dim) {
     fclose(f);
     return fail(s, SISPH_EINVAL, "checkpoint does not match this handle");
   }
@@ -1087,15 +1227,28 @@ int sisph_load(sisph_t s, const char *path) {
     int rc = sisph_set(s, fld, buf.data());
     if (rc) { fclose(f); return rc; }
   }
+  for (int k = 0; k < s->dim; ++k) {
+    if (fread(buf.data(), sizeof(double), buf.size(), f) != buf.size()) { fclose(f); return fail(s, SISPH_EINVAL, "short checkpoint"); }
+    int rc = copy_in(s, buf.data(), s->S.xref[k]);
+    if (rc) { fclose(f); return rc; }
+  }
   std::vector<double> pr(s->ncases);
   std::vector<int> ps(s->ncases);
+  int32_t pending = 0;
   ok = fread(pr.data(), sizeof(double), pr.size(), f) == pr.size() &&
-       fread(ps.data(), sizeof(int), ps.size(), f) == ps.size();
+       fread(ps.data(), sizeof(int), ps.size(), f) == ps.size() && fread(&pending, sizeof(pending), 1, f) == 1;
   fclose(f);
   if (!ok) return fail(s, SISPH_EINVAL, "short checkpoint");
-  cudaMemcpy(s->S.pref, pr.data(), s->ncases * sizeof(double), cudaMemcpyHostToDevice);
-  cudaMemcpy(s->S.pref_set, ps.data(), s->ncases * sizeof(int), cudaMemcpyHostToDevice);
-  return SISPH_OK;
+  cudaError_t e = cudaMemcpy(s->S.pref, pr.data(), s->ncases * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->S.pref_set, ps.data(), s->ncases * sizeof(int), cudaMemcpyHostToDevice);
+  // sort and skin lists as they were at the saved rebuild positions (or at
+  // the current ones if a rebuild was pending), then the refresh the saved
+  // run would have made next
+  if (e == cudaSuccess) e = force_rebuild(s, pending ? 1 : 2);
+  if (e == cudaSuccess) e = do_refresh(s, 0, false);
+  if (e == cudaSuccess) e = do_refresh(s, 0, false);
+  if (e != cudaSuccess) return cuda_fail(s, e, "load");
+  return check_status(s, false);
 }
 
 }  // extern "C"

@@ -1,7 +1,25 @@
-// Cell-list neighbour search: Morton-ordered counting sort of the particles
-// and ELL neighbour lists.  The paper leaves the search to PySPH (Sec. 3.3);
-// N(i) = {j : |r_ij|^2 < (3h)^2} with the minimum image in periodic
-// directions, i itself included (support of the quintic spline, Sec. 2.1).
+// Cell-list neighbour search with Verlet skin lists.  The paper leaves the
+// search to PySPH (Sec. 3.3); N(i) = {j : |r_ij|^2 < (3h)^2} with the minimum
+// image in periodic directions, i itself included (support of the quintic
+// spline, Sec. 2.1).
+//
+// One refresh of the lists at positions X (r^n, or r* after stage 1):
+//  check    a case whose fluid moved more than s/2 since its last rebuild
+//           (or every case, on a forced refresh) is marked for a rebuild;
+//  rebuild  only when some case is marked (every kernel returns at once
+//           otherwise): Morton-ordered counting sort of the particle set --
+//           marked cases binned at X, the others at their last rebuild
+//           positions, which leaves them where they are -- gather, copy back;
+//           then, for the marked cases, the skin list: every j within 3h + s
+//           of i at the rebuild positions;
+//  finish   without a rebuild, the stage-1 outputs and FP32 mirrors are
+//           committed in place; the FP32 relative positions are brought to X;
+//           then N(i) is filtered exactly out of the skin list at X.
+// The order of the particles and the skin lists are a function of the rebuild
+// positions alone, so a state restored with them (force mode 2: rebuild every
+// case at its stored rebuild positions) continues bit-identically.
+// Between rebuilds no particle has moved more than s/2 from its rebuild
+// position, so every pair now closer than 3h was closer than 3h + s then.
 #include "sisph_internal.h"
 
 namespace sisph {
@@ -27,10 +45,9 @@ __device__ __forceinline__ unsigned spread3(unsigned x) {
 template <int DIM>
 __device__ __forceinline__ void cell_of(const CaseDev &P, const double xi[3], int c[3]) {
   c[2] = 0;
-#pragma unroll
-  for (int k = 0; k < DIM; ++k) {
-    // cells are 3h (1 + 1e-9) or wider, so a product with 1/L_c instead of a
-    // quotient still leaves any pair closer than 3h in adjacent cells
+  _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
+    // cells are (3h + s)(1 + 1e-9) or wider, so a product with 1/L_c instead
+    // of a quotient still leaves any pair closer than 3h + s in adjacent cells
     double t = floor((xi[k] - P.lo[k]) * P.inv_lc[k]);
     int ci;
     if (!(t >= 0.0)) ci = 0;                       // also catches NaN
@@ -38,6 +55,16 @@ __device__ __forceinline__ void cell_of(const CaseDev &P, const double xi[3], in
     else ci = int(t);
     c[k] = ci;
   }
+}
+
+// Rebuild cell of a particle, 21 bits per axis.
+__device__ __forceinline__ long long pack_cell(const int c[3]) {
+  return (long long)c[0] | ((long long)c[1] << 21) | ((long long)c[2] << 42);
+}
+__device__ __forceinline__ void unpack_cell(long long v, int c[3]) {
+  c[0] = int(v & 0x1fffff);
+  c[1] = int((v >> 21) & 0x1fffff);
+  c[2] = int((v >> 42) & 0x1fffff);
 }
 
 template <int DIM>
@@ -54,14 +81,104 @@ __device__ __forceinline__ const Tile &tile_of(const State &S, int b) {
   return b < S.nft ? S.ftiles[b] : S.wtiles[b - S.nft];
 }
 
+// A cell on the edge of a non-periodic grid holds the particles that left
+// the box (clamped into it), whose cell-relative coordinates can be large.
+template <int DIM>
+__device__ __forceinline__ bool edge_cell(const CaseDev &P, const int c[3]) {
+  bool e = false;
+  _Pragma("unroll") for (int k = 0; k < DIM; ++k)
+    e |= !P.per[k] && (c[k] == 0 || c[k] == P.nc[k] - 1);
+  return e;
+}
+
+// FP32 position relative to the origin of the particle's rebuild cell (the
+// minimum image of it in periodic directions, since a particle may have
+// wrapped since the rebuild), and its mass: the neighbour tests use it, and
+// so do all MIXED neighbour sums.
+template <int DIM>
+__device__ __forceinline__ float4 rel_pos(const CaseDev &P, const double xi[3], long long cell, double m) {
+  int c[3];
+  unpack_cell(cell, c);
+  float rel[3] = {0.f, 0.f, 0.f};
+  _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
+    double d = xi[k] - (P.lo[k] + double(c[k]) * P.lc[k]);
+    if (P.per[k]) {
+      if (d > P.half[k]) d -= P.L[k];
+      else if (d < -P.half[k]) d += P.L[k];
+    }
+    rel[k] = float(d);
+  }
+  return make_float4(rel[0], rel[1], rel[2], float(m));
+}
+
+// ---------------------------------------------------------------------------
+// check
+// ---------------------------------------------------------------------------
+// Mark case c for a rebuild; count the rebuilds per case and the refreshes
+// that rebuild anything (last counter).
+__device__ __forceinline__ void mark(const State &S, int c) {
+  if (atomicOr(S.need + c, 1) == 0) atomicAdd(reinterpret_cast<unsigned long long *>(S.nreb + c), 1ull);
+  if (atomicOr(S.anyneed, 1) == 0)
+    atomicAdd(reinterpret_cast<unsigned long long *>(S.nreb + S.ncases), 1ull);
+}
+
+// Binned at the current positions X: a marked case, unless the refresh
+// restores the stored rebuild positions.
+__device__ __forceinline__ bool at_x(const State &S, int c) { return S.need[c] != 0 && *S.force != 2; }
+
+template <int DIM>
+__global__ void k_check(State S, const double *__restrict__ x0, const double *__restrict__ x1,
+                        const double *__restrict__ x2) {
+  const Tile &t = tile_of(S, blockIdx.x);
+  const int c = t.c;
+  if (*S.force) {
+    if (threadIdx.x == 0) mark(S, c);
+    return;
+  }
+  if (t.kind != 0) return;   // walls never move
+  const int i = t.beg + threadIdx.x;
+  bool moved = false;
+  if (i < t.end) {
+    const CaseDev &P = S.cases[c];
+    const double X[3] = {x0[i], x1[i], DIM == 3 ? x2[i] : 0.0};
+    double d2 = 0.0;
+    _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
+      double d = X[k] - S.xref[k][i];
+      if (P.per[k]) {
+        if (d > P.half[k]) d -= P.L[k];
+        else if (d < -P.half[k]) d += P.L[k];
+      }
+      d2 += d * d;
+    }
+    moved = !(d2 <= P.skin_half2);   // also catches NaN
+  }
+  if (__syncthreads_or(moved) && threadIdx.x == 0) mark(S, c);
+}
+
+// ---------------------------------------------------------------------------
+// rebuild: counting sort
+// ---------------------------------------------------------------------------
+__global__ void k_zero_hist(State S, int count_on_device) {
+  if (!*S.anyneed) return;
+  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (count_on_device && q == 0) atomicAdd(reinterpret_cast<unsigned long long *>(S.nbody), 1ull);
+  if (q <= S.K) S.hist[q] = 0u;
+}
+
+// Marked cases are binned at X, the others at their rebuild positions.
 template <int DIM>
 __global__ void k_keys(State S, const double *__restrict__ p0, const double *__restrict__ p1,
                        const double *__restrict__ p2) {
+  if (!*S.anyneed) return;
   const Tile &t = tile_of(S, blockIdx.x);
   int i = t.beg + threadIdx.x;
   if (i >= t.end) return;
   const CaseDev &P = S.cases[t.c];
-  double xi[3] = {p0[i], p1[i], DIM == 3 ? p2[i] : 0.0};
+  const bool mv = at_x(S, t.c);
+  double xi[3];
+  xi[0] = mv ? p0[i] : S.xref[0][i];
+  xi[1] = mv ? p1[i] : S.xref[1][i];
+  xi[2] = DIM == 3 ? (mv ? p2[i] : S.xref[2][i]) : 0.0;
   int c[3];
   cell_of<DIM>(P, xi, c);
   long long key = P.key_base + (long long)t.kind * P.slots + cell_key<DIM>(P, c);
@@ -77,8 +194,7 @@ constexpr int kScanChunk = kScanThreads * kScanItems;
 __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned *sh, unsigned *total) {
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
+  _Pragma("unroll") for (int o = 1; o < 32; o <<= 1) {
     unsigned y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
@@ -86,8 +202,7 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned *sh, un
   __syncthreads();
   if (w == 0) {
     unsigned s = (lane < int(blockDim.x >> 5)) ? sh[lane] : 0u;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
+    _Pragma("unroll") for (int o = 1; o < 32; o <<= 1) {
       unsigned y = __shfl_up_sync(0xffffffffu, s, o);
       if (lane >= o) s += y;
     }
@@ -99,27 +214,27 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned *sh, un
   return base + x - v;
 }
 
-__global__ void k_scan_chunks(unsigned *a, long long n, unsigned *bsum) {
+__global__ void k_scan_chunks(const int *flag, unsigned *a, long long n, unsigned *bsum) {
+  if (!*flag) return;
   __shared__ unsigned sh[32];
   long long base = (long long)blockIdx.x * kScanChunk + (long long)threadIdx.x * kScanItems;
   unsigned v[kScanItems];
   unsigned s = 0;
-#pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
+  _Pragma("unroll") for (int k = 0; k < kScanItems; ++k) {
     v[k] = (base + k < n) ? a[base + k] : 0u;
     s += v[k];
   }
   unsigned tot;
   unsigned ex = block_excl_scan(s, sh, &tot);
-#pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
+  _Pragma("unroll") for (int k = 0; k < kScanItems; ++k) {
     if (base + k < n) a[base + k] = ex;
     ex += v[k];
   }
   if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
 }
 
-__global__ void k_scan_single(unsigned *a, int n) {
+__global__ void k_scan_single(const int *flag, unsigned *a, int n) {
+  if (!*flag) return;
   __shared__ unsigned sh[32];
   __shared__ unsigned carry;
   if (threadIdx.x == 0) carry = 0;
@@ -128,15 +243,13 @@ __global__ void k_scan_single(unsigned *a, int n) {
     int idx = base + threadIdx.x * kScanItems;
     unsigned v[kScanItems];
     unsigned s = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
+    _Pragma("unroll") for (int k = 0; k < kScanItems; ++k) {
       v[k] = (idx + k < n) ? a[idx + k] : 0u;
       s += v[k];
     }
     unsigned tot;
     unsigned ex = block_excl_scan(s, sh, &tot) + carry;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
+    _Pragma("unroll") for (int k = 0; k < kScanItems; ++k) {
       if (idx + k < n) a[idx + k] = ex;
       ex += v[k];
     }
@@ -146,15 +259,16 @@ __global__ void k_scan_single(unsigned *a, int n) {
   }
 }
 
-__global__ void k_scan_add(unsigned *a, long long n, const unsigned *bsum) {
+__global__ void k_scan_add(const int *flag, unsigned *a, long long n, const unsigned *bsum) {
+  if (!*flag) return;
   long long base = (long long)blockIdx.x * kScanChunk + (long long)threadIdx.x * kScanItems;
   unsigned add = bsum[blockIdx.x];
-#pragma unroll
-  for (int k = 0; k < kScanItems; ++k)
+  _Pragma("unroll") for (int k = 0; k < kScanItems; ++k)
     if (base + k < n) a[base + k] += add;
 }
 
 __global__ void k_scatter(State S) {
+  if (!*S.anyneed) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= S.n) return;
   unsigned dst = S.hist[S.key[i]] + S.slot[i];
@@ -163,18 +277,19 @@ __global__ void k_scatter(State S) {
 
 // Order each cell by original particle index, so the sorted order (and with
 // it every neighbour-sum order) is independent of atomic arrival order.
-__global__ void k_cellsort(State S, const int *__restrict__ uid) {
+__global__ void k_cellsort(State S) {
+  if (!*S.anyneed) return;
   long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= S.K) return;
   unsigned beg = S.hist[q], end = S.hist[q + 1];
   if (end - beg < 2) return;
   for (unsigned a = beg + 1; a < end; ++a) {
     int pa = S.perm[a];
-    int ka = uid[pa];
+    int ka = S.uid[pa];
     unsigned b = a;
     while (b > beg) {
       int pb = S.perm[b - 1];
-      if (uid[pb] <= ka) break;
+      if (S.uid[pb] <= ka) break;
       S.perm[b] = pb;
       --b;
     }
@@ -182,113 +297,121 @@ __global__ void k_cellsort(State S, const int *__restrict__ uid) {
   }
 }
 
-// Gather every per-particle stream into the new order.  mode 0: positions
-// from x (build at r^n); mode 1: positions from the stage-1 output r*, the
-// old positions become r^n and the velocity comes from u*.
+// Gather every per-particle stream into the new order (B buffers).  mode 0:
+// positions from x (refresh at r^n); mode 1: positions from the stage-1
+// output r*, the old positions become r^n and the velocity comes from u*.
+// The rebuild position follows the particle; a marked case takes its
+// current position as the new one.
 template <int DIM>
 __global__ void k_gather(State S, int mode, int gather_static) {
+  if (!*S.anyneed) return;
   int dst = blockIdx.x * blockDim.x + threadIdx.x;
   if (dst >= S.n) return;
-  int src = S.perm[dst];
-  double uu[3] = {0, 0, 0}, tt[3] = {0, 0, 0};
-#pragma unroll
-  for (int k = 0; k < DIM; ++k) {
+  const int src = S.perm[dst];
+  const int c = S.case_of[dst];
+  const bool mv = at_x(S, c);
+  double uu[3] = {0, 0, 0}, tt[3] = {0, 0, 0}, xr[3] = {0, 0, 0};
+  _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
+    double xnew;
     if (mode == 0) {
-      S.bx[k][dst] = S.x[k][src];
+      xnew = S.x[k][src];
       S.bxn[k][dst] = S.xn[k][src];
       uu[k] = S.u[k][src];
     } else {
-      S.bx[k][dst] = S.xs[k][src];
+      xnew = S.xs[k][src];
       S.bxn[k][dst] = S.x[k][src];
       uu[k] = S.us[k][src];
     }
+    S.bx[k][dst] = xnew;
+    xr[k] = mv ? xnew : S.xref[k][src];
+    S.bxref[k][dst] = xr[k];
     tt[k] = S.ut[k][src];
     S.bu[k][dst] = uu[k];
     S.but[k][dst] = tt[k];
   }
-  double r = S.rho[src];
+  const double r = S.rho[src];
   S.bm[dst] = S.m[src];
   S.brho[dst] = r;
   S.bp[dst] = S.p[src];
   S.buid[dst] = S.uid[src];
+  int cc[3];
+  cell_of<DIM>(S.cases[c], xr, cc);
+  S.bcell[dst] = pack_cell(cc);
   if (gather_static) {
     // walls only move once, at the first sort: carry their prescribed velocity
-#pragma unroll
-    for (int k = 0; k < 3; ++k) S.nstar[k][dst] = S.uw[k][src];
+    _Pragma("unroll") for (int k = 0; k < 3; ++k) S.nstar[k][dst] = S.uw[k][src];
   }
   if (S.mixed) {
     S.vf4[dst] = make_float4(float(uu[0]), float(uu[1]), float(uu[2]), float(r));
     S.utf4[dst] = make_float4(float(tt[0]), float(tt[1]), float(tt[2]), 0.f);
     S.pf[dst] = float(S.p[src]);
   }
-  // FP32 position relative to the particle's own cell, and its mass: the
-  // neighbour build pre-tests pairs on it, the MIXED sums use it throughout
-  const CaseDev &P = S.cases[S.case_of[dst]];
-  double xi[3] = {0.0, 0.0, 0.0};
-  _Pragma("unroll") for (int k = 0; k < DIM; ++k) xi[k] = S.bx[k][dst];
-  int c[3];
-  cell_of<DIM>(P, xi, c);
-  float rel[3] = {0.f, 0.f, 0.f};
-  _Pragma("unroll") for (int k = 0; k < DIM; ++k) rel[k] = float(xi[k] - (P.lo[k] + double(c[k]) * P.lc[k]));
-  S.pf4[dst] = make_float4(rel[0], rel[1], rel[2], float(S.m[src]));
 }
 
-__global__ void k_copy_static(State S) {
+// Copy the gathered streams back into the state; the FP32 relative
+// positions are taken at the rebuild positions for the skin lists.
+template <int DIM>
+__global__ void k_copyback(State S, int gather_static) {
+  if (!*S.anyneed) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= S.n) return;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) S.uw[k][i] = S.nstar[k][i];
+  double xr[3] = {0.0, 0.0, 0.0};
+  _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
+    xr[k] = S.bxref[k][i];
+    S.x[k][i] = S.bx[k][i];
+    S.xn[k][i] = S.bxn[k][i];
+    S.u[k][i] = S.bu[k][i];
+    S.ut[k][i] = S.but[k][i];
+    S.xref[k][i] = xr[k];
+  }
+  const double m = S.bm[i];
+  const long long cell = S.bcell[i];
+  S.m[i] = m;
+  S.rho[i] = S.brho[i];
+  S.p[i] = S.bp[i];
+  S.uid[i] = S.buid[i];
+  S.cell[i] = cell;
+  if (gather_static) {
+    _Pragma("unroll") for (int k = 0; k < 3; ++k) S.uw[k][i] = S.nstar[k][i];
+  }
+  S.pf4[i] = rel_pos<DIM>(S.cases[S.case_of[i]], xr, cell, m);
 }
 
-// A cell on the edge of a non-periodic grid holds the particles that left
-// the box (clamped into it), whose cell-relative coordinates can be large.
+// ---------------------------------------------------------------------------
+// rebuild: skin lists of the marked cases, every j within 3h + s of i (FP32
+// test on cell-relative coordinates with a relative margin of 2e-4 on the
+// squared cutoff, which covers its rounding; FP64 for pairs touching an edge
+// cell), all at the rebuild positions.  The list only has to contain N(i)
+// at every later refresh before the next rebuild.
+// ---------------------------------------------------------------------------
 template <int DIM>
-__device__ __forceinline__ bool edge_cell(const CaseDev &P, const int c[3]) {
-  bool e = false;
-  _Pragma("unroll") for (int k = 0; k < DIM; ++k)
-    e |= !P.per[k] && (c[k] == 0 || c[k] == P.nc[k] - 1);
-  return e;
-}
-
-// One thread per particle: scan the 3^d stencil of cells (fluid block, then
-// wall block of each cell) and append every j with |r_ij|^2 < (3h)^2 to the
-// ELL row.  Each candidate is first tested in FP32 on cell-relative
-// coordinates (error below 1e-5 of (3h)^2); a pair within a relative band of
-// 1e-4 around the cutoff is set aside and decided after the cell loop by the
-// exact unfused FP64 test, so the set equals the FP64 definition and a warp
-// pays for as many FP64 tests as its busiest lane (lattice inputs put many
-// pairs exactly on the cutoff).  Edge cells of a non-periodic grid take the
-// FP64 test directly.
-template <int DIM>
-__global__ void __launch_bounds__(256) k_build(State S) {
-  constexpr int kBand = DIM == 3 ? 48 : 16;
+__global__ void __launch_bounds__(256) k_skin(State S) {
   const Tile &t = tile_of(S, blockIdx.x);
-  int i = t.beg + threadIdx.x;
+  if (!S.need[t.c]) return;
+  const int i = t.beg + threadIdx.x;
   if (i >= t.end) return;
   const CaseDev &P = S.cases[t.c];
-  double xi[3] = {S.x[0][i], S.x[1][i], DIM == 3 ? S.x[2][i] : 0.0};
   int c[3];
-  cell_of<DIM>(P, xi, c);
+  unpack_cell(S.cell[i], c);
   const bool own_edge = edge_cell<DIM>(P, c);
+  const double xi[3] = {S.xref[0][i], S.xref[1][i], DIM == 3 ? S.xref[2][i] : 0.0};
   const float4 pi = S.pf4[i];
   const float lx = P.lcf[0], ly = P.lcf[1], lz = P.lcf[2];
-  const float cut2f = float(P.cut2);
-  const float lo_band = cut2f * (1.0f - 1e-4f), hi_band = cut2f * (1.0f + 1e-4f);
+  const float cut2f = float(P.cut_s2) * (1.0f + 2e-4f);
+  const double cut2d = P.cut_s2 * (1.0 + 2e-4);
   const int zr = (DIM == 3) ? 1 : 0;
+  const long long nn = S.n;
   int cnt = 0;
   bool over = false;
-  const long long nn = S.n;
-  unsigned band[kBand];
-  int nband = 0;
   auto append = [&](unsigned entry) {
-    if (cnt < S.cap) S.nbr[(long long)cnt * nn + i] = entry;
+    if (cnt < S.scap) S.snbr[(long long)cnt * nn + i] = entry;
     else over = true;
     ++cnt;
   };
   for (int oz = -zr; oz <= zr; ++oz) {
     for (int oy = -1; oy <= 1; ++oy) {
       for (int ox = -1; ox <= 1; ++ox) {
-        int o[3] = {ox, oy, oz};
+        const int o[3] = {ox, oy, oz};
         int cn[3] = {c[0], c[1], c[2]};
         bool skip = false;
         _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
@@ -303,15 +426,15 @@ __global__ void __launch_bounds__(256) k_build(State S) {
         const bool exact_all = own_edge || edge_cell<DIM>(P, cn);
         const unsigned code = stencil_code(ox, oy, oz) << kCodeShift;
         const float fx = pi.x - float(ox) * lx, fy = pi.y - float(oy) * ly, fz = pi.z - float(oz) * lz;
-        long long m = cell_key<DIM>(P, cn);
+        const long long m = cell_key<DIM>(P, cn);
         for (int kind = 0; kind < 2; ++kind) {
           if (kind == 1 && P.nw == 0) break;
-          long long q = P.key_base + (long long)kind * P.slots + m;
+          const long long q = P.key_base + (long long)kind * P.slots + m;
           const unsigned beg = S.hist[q], end = S.hist[q + 1];
           if (exact_all) {
             for (unsigned j = beg; j < end; ++j) {
               double d[3];
-              if (pair_d<DIM>(P, xi, S.x, int(j), d) < P.cut2) append(j | code);
+              if (pair_d<DIM>(P, xi, S.xref, int(j), d) < cut2d) append(j | code);
             }
             continue;
           }
@@ -322,33 +445,134 @@ __global__ void __launch_bounds__(256) k_build(State S) {
             _Pragma("unroll") for (int u = 0; u < 8; ++u)
               pj[u] = j0 + u < end ? S.pf4[j0 + u] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
             _Pragma("unroll") for (int u = 0; u < 8; ++u) {
-              const unsigned j = j0 + u;
               float dx = fx - pj[u].x, dy = fy - pj[u].y;
               float r2f = dx * dx + dy * dy;
               if (DIM == 3) {
                 float dz = fz - pj[u].z;
                 r2f += dz * dz;
               }
-              if (r2f < lo_band) {
-                append(j | code);
-              } else if (r2f <= hi_band) {
-                if (nband < kBand) {
-                  band[nband++] = j | code;
-                } else {
-                  double d[3];
-                  if (pair_d<DIM>(P, xi, S.x, int(j), d) < P.cut2) append(j | code);
-                }
-              }
+              if (r2f < cut2f) append((j0 + u) | code);
             }
           }
         }
       }
     }
   }
-  for (int b = 0; b < nband; ++b) {
-    double d[3];
-    if (pair_d<DIM>(P, xi, S.x, int(band[b] & kIdxMask), d) < P.cut2) append(band[b]);
+  if (over) {
+    atomicOr(S.err, kErrCapacity);
+    cnt = S.scap;
   }
+  S.sncnt[i] = cnt;
+}
+
+// ---------------------------------------------------------------------------
+// finish
+// ---------------------------------------------------------------------------
+// Without a rebuild the order is unchanged: mode 1 commits the stage-1
+// outputs in place (r^n <- r, r <- r*, u <- u*) and the FP32 mirrors are
+// refreshed from the FP64 state, as the gather would have done.  Always: the
+// FP32 relative positions at X.
+template <int DIM>
+__global__ void k_sync(State S, int mode) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S.n) return;
+  const CaseDev &P = S.cases[S.case_of[i]];
+  double xi[3] = {0, 0, 0};
+  if (*S.anyneed) {
+    _Pragma("unroll") for (int k = 0; k < DIM; ++k) xi[k] = S.x[k][i];
+    S.pf4[i] = rel_pos<DIM>(P, xi, S.cell[i], S.m[i]);
+    return;
+  }
+  double uu[3] = {0, 0, 0}, tt[3] = {0, 0, 0};
+  _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
+    if (mode == 1) {
+      xi[k] = S.xs[k][i];
+      S.xn[k][i] = S.x[k][i];
+      S.x[k][i] = xi[k];
+      uu[k] = S.us[k][i];
+      S.u[k][i] = uu[k];
+    } else {
+      xi[k] = S.x[k][i];
+      uu[k] = S.u[k][i];
+    }
+    tt[k] = S.ut[k][i];
+  }
+  if (S.mixed) {
+    S.vf4[i] = make_float4(float(uu[0]), float(uu[1]), float(uu[2]), float(S.rho[i]));
+    S.utf4[i] = make_float4(float(tt[0]), float(tt[1]), float(tt[2]), 0.f);
+    S.pf[i] = float(S.p[i]);
+  }
+  S.pf4[i] = rel_pos<DIM>(P, xi, S.cell[i], S.m[i]);
+}
+
+// N(i) out of the skin list at the current positions: FP32 test on
+// cell-relative coordinates (error below 1e-5 of (3h)^2); a pair within a
+// relative band of 1e-4 of the cutoff is set aside and decided after the
+// loop by the exact unfused FP64 test, so the set equals the FP64 definition
+// and a warp pays for as many FP64 tests as its busiest lane (lattice inputs
+// put many pairs exactly on the cutoff).  Pairs touching an edge cell take
+// the FP64 test directly.  The list keeps the skin list's order.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_filter(State S) {
+  constexpr int kBand = DIM == 3 ? 48 : 16;
+  const Tile &t = tile_of(S, blockIdx.x);
+  const int i = t.beg + threadIdx.x;
+  if (i >= t.end) return;
+  const CaseDev &P = S.cases[t.c];
+  int c[3];
+  unpack_cell(S.cell[i], c);
+  const bool own_edge = edge_cell<DIM>(P, c);
+  const float4 pi = S.pf4[i];
+  const float lc[3] = {P.lcf[0], P.lcf[1], P.lcf[2]};
+  const float cut2f = float(P.cut2);
+  const float lo_band = cut2f * (1.0f - 1e-4f), hi_band = cut2f * (1.0f + 1e-4f);
+  const long long nn = S.n;
+  const int scnt = S.sncnt[i];
+  int cnt = 0;
+  bool over = false;
+  unsigned band[kBand];
+  int nband = 0;
+  auto append = [&](unsigned entry) {
+    if (cnt < S.cap) S.nbr[(long long)cnt * nn + i] = entry;
+    else over = true;
+    ++cnt;
+  };
+  auto exact = [&](unsigned entry) {
+    const double xi[3] = {S.x[0][i], S.x[1][i], DIM == 3 ? S.x[2][i] : 0.0};
+    double d[3];
+    return pair_d<DIM>(P, xi, S.x, int(entry & kIdxMask), d) < P.cut2;
+  };
+  for (int q0 = 0; q0 < scnt; q0 += 8) {
+    unsigned e[8];
+    _Pragma("unroll") for (int u = 0; u < 8; ++u)
+      e[u] = q0 + u < scnt ? S.snbr[(long long)(q0 + u) * nn + i] : (unsigned(i) | (stencil_code(0, 0, 0) << kCodeShift));
+    float4 pj[8];
+    _Pragma("unroll") for (int u = 0; u < 8; ++u) pj[u] = S.pf4[e[u] & kIdxMask];
+    _Pragma("unroll") for (int u = 0; u < 8; ++u) {
+      if (q0 + u >= scnt) continue;
+      const unsigned code = e[u] >> kCodeShift;
+      bool edge = own_edge;
+      if (!edge) {
+        const int cj[3] = {c[0] + int(code & 3u) - 1, c[1] + int((code >> 2) & 3u) - 1,
+                           c[2] + int(code >> 4) - 1};
+        edge = edge_cell<DIM>(P, cj);
+      }
+      if (edge) {
+        if (exact(e[u])) append(e[u]);
+        continue;
+      }
+      float d[3];
+      const float r2f = pair_f<DIM>(lc, pi, pj[u], code, d);
+      if (r2f < lo_band) {
+        append(e[u]);
+      } else if (r2f <= hi_band) {
+        if (nband < kBand) band[nband++] = e[u];
+        else if (exact(e[u])) append(e[u]);
+      }
+    }
+  }
+  for (int b = 0; b < nband; ++b)
+    if (exact(band[b])) append(band[b]);
   if (over) {
     atomicOr(S.err, kErrCapacity);
     cnt = S.cap;
@@ -356,48 +580,79 @@ __global__ void __launch_bounds__(256) k_build(State S) {
   S.ncnt[i] = cnt;
 }
 
-static cudaError_t scan(const State &S, const Launch &L, unsigned *bsum) {
-  long long n = S.K + 1;
-  int nb = int((n + kScanChunk - 1) / kScanChunk);
-  k_scan_chunks<<<nb, kScanThreads, 0, L.stream>>>(S.hist, n, bsum);
-  k_scan_single<<<1, kScanThreads, 0, L.stream>>>(bsum, nb);
-  k_scan_add<<<nb, kScanThreads, 0, L.stream>>>(S.hist, n, bsum);
+// The rebuild group of a captured step sits in a conditional graph node whose
+// condition is whether any case needs a rebuild.
+__global__ void k_set_conditional(cudaGraphConditionalHandle h, const int *anyneed) {
+  cudaGraphSetConditional(h, *anyneed ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_set_conditional(const State &S, const Launch &L, cudaGraphConditionalHandle h) {
+  k_set_conditional<<<1, 1, 0, L.stream>>>(h, S.anyneed);
+  if (L.after) L.after(L.ctx, "setcond", 0.0, 1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sort(const State &S, const Launch &L, const double *const pos[3], int gather_mode,
-                        bool gather_static) {
-  int nt = S.nft + S.nwt;
+cudaError_t launch_refresh_check(const State &S, const Launch &L, int mode) {
+  const int nt = S.nft + S.nwt;
+  const double *const *pos = mode == 0 ? S.x : S.xs;
+  cudaMemsetAsync(S.need, 0, sizeof(int) * size_t(S.ncases), L.stream);
+  cudaMemsetAsync(S.anyneed, 0, sizeof(int), L.stream);
+  if (L.before) L.before(L.ctx, "check");
+  if (S.dim == 2) k_check<2><<<nt, S.T, 0, L.stream>>>(S, pos[0], pos[1], pos[2]);
+  else k_check<3><<<nt, S.T, 0, L.stream>>>(S, pos[0], pos[1], pos[2]);
+  if (L.after) L.after(L.ctx, "check", double(S.n), 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refresh_rebuild(const State &S, const Launch &L, int mode, bool gather_static,
+                                   bool count_on_device) {
+  const int nt = S.nft + S.nwt;
+  const int nb = (S.n + 255) / 256;
+  const double *const *pos = mode == 0 ? S.x : S.xs;
+  const int gs = gather_static ? 1 : 0;
   if (L.before) L.before(L.ctx, "sort");
-  cudaMemsetAsync(S.hist, 0, sizeof(unsigned) * size_t(S.K + 1), L.stream);
+  k_zero_hist<<<int((S.K + 1 + 255) / 256), 256, 0, L.stream>>>(S, count_on_device ? 1 : 0);
   if (S.dim == 2) k_keys<2><<<nt, S.T, 0, L.stream>>>(S, pos[0], pos[1], pos[2]);
   else k_keys<3><<<nt, S.T, 0, L.stream>>>(S, pos[0], pos[1], pos[2]);
   // block sums live after the K+1 histogram entries
-  unsigned *bsum = S.hist + (S.K + 1);
-  cudaError_t e = scan(S, L, bsum);
-  if (e != cudaSuccess) return e;
-  int nb = (S.n + 255) / 256;
+  const long long nh = S.K + 1;
+  const int ns = int((nh + kScanChunk - 1) / kScanChunk);
+  unsigned *bsum = S.hist + nh;
+  k_scan_chunks<<<ns, kScanThreads, 0, L.stream>>>(S.anyneed, S.hist, nh, bsum);
+  k_scan_single<<<1, kScanThreads, 0, L.stream>>>(S.anyneed, bsum, ns);
+  k_scan_add<<<ns, kScanThreads, 0, L.stream>>>(S.anyneed, S.hist, nh, bsum);
   k_scatter<<<nb, 256, 0, L.stream>>>(S);
-  int kb = int((S.K + 255) / 256);
-  k_cellsort<<<kb, 256, 0, L.stream>>>(S, S.uid);
-  if (S.dim == 2) k_gather<2><<<nb, 256, 0, L.stream>>>(S, gather_mode, gather_static ? 1 : 0);
-  else k_gather<3><<<nb, 256, 0, L.stream>>>(S, gather_mode, gather_static ? 1 : 0);
-  if (L.after) L.after(L.ctx, "sort", double(S.n), 7);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_build(const State &S, const Launch &L) {
-  int nt = S.nft + S.nwt;
+  k_cellsort<<<int((S.K + 255) / 256), 256, 0, L.stream>>>(S);
+  if (S.dim == 2) {
+    k_gather<2><<<nb, 256, 0, L.stream>>>(S, mode, gs);
+    k_copyback<2><<<nb, 256, 0, L.stream>>>(S, gs);
+  } else {
+    k_gather<3><<<nb, 256, 0, L.stream>>>(S, mode, gs);
+    k_copyback<3><<<nb, 256, 0, L.stream>>>(S, gs);
+  }
+  if (L.after) L.after(L.ctx, "sort", double(S.n), 9);
   if (L.before) L.before(L.ctx, "build");
-  if (S.dim == 2) k_build<2><<<nt, S.T, 0, L.stream>>>(S);
-  else k_build<3><<<nt, S.T, 0, L.stream>>>(S);
+  if (S.dim == 2) k_skin<2><<<nt, S.T, 0, L.stream>>>(S);
+  else k_skin<3><<<nt, S.T, 0, L.stream>>>(S);
   if (L.after) L.after(L.ctx, "build", double(S.n), 1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_copy_static(const State &S, const Launch &L) {
-  int nb = (S.n + 255) / 256;
-  k_copy_static<<<nb, 256, 0, L.stream>>>(S);
+cudaError_t launch_refresh_finish(const State &S, const Launch &L, int mode) {
+  const int nt = S.nft + S.nwt;
+  const int nb = (S.n + 255) / 256;
+  if (L.before) L.before(L.ctx, "sync");
+  if (S.dim == 2) k_sync<2><<<nb, 256, 0, L.stream>>>(S, mode);
+  else k_sync<3><<<nb, 256, 0, L.stream>>>(S, mode);
+  if (L.after) L.after(L.ctx, "sync", double(S.n), 1);
+  if (L.before) L.before(L.ctx, "filter");
+  if (S.dim == 2) k_filter<2><<<nt, S.T, 0, L.stream>>>(S);
+  else k_filter<3><<<nt, S.T, 0, L.stream>>>(S);
+  if (L.after) L.after(L.ctx, "filter", double(S.n), 1);
+  cudaMemsetAsync(S.force, 0, sizeof(int), L.stream);
   return cudaGetLastError();
 }
 

@@ -556,6 +556,7 @@ __global__ void k_scatter_field(State S, const void *src, int is_float, int stri
   if (i >= S.n) return;
   double v;
   if (stride_f4) v = double((&static_cast<const float4 *>(src)[i].x)[comp]);
+  else if (is_float == 2) v = double(static_cast<const int *>(src)[i]);
   else if (is_float) v = double(static_cast<const float *>(src)[i]);
   else v = static_cast<const double *>(src)[i];
   dst[S.uid[i]] = v;
@@ -605,13 +606,17 @@ cudaError_t launch_ghost(const State &S, const Launch &L, int slip_stage) {
 }
 
 cudaError_t launch_stage1(const State &S, const Launch &L) {
-  if (L.before) L.before(L.ctx, "stage1");
-  if (S.nft) DISPATCH(S, k_stage1, <<<S.nft, S.T, 0, L.stream>>>(S));
+  if (S.nft) {
+    if (L.before) L.before(L.ctx, "stage1");
+    DISPATCH(S, k_stage1, <<<S.nft, S.T, 0, L.stream>>>(S));
+    if (L.after) L.after(L.ctx, "stage1", double(S.nf), 1);
+  }
   if (S.nwt) {
+    if (L.before) L.before(L.ctx, "stage1_walls");
     if (S.dim == 2) k_stage1_walls<2><<<S.nwt, S.T, 0, L.stream>>>(S);
     else k_stage1_walls<3><<<S.nwt, S.T, 0, L.stream>>>(S);
+    if (L.after) L.after(L.ctx, "stage1_walls", double(S.nw), 1);
   }
-  if (L.after) L.after(L.ctx, "stage1", double(S.nf), (S.nft ? 1 : 0) + (S.nwt ? 1 : 0));
   return cudaGetLastError();
 }
 

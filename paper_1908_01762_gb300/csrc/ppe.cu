@@ -454,8 +454,8 @@ __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
 }
 
 cudaError_t launch_ppe_setup(const State &S, const Launch &L) {
-  if (L.before) L.before(L.ctx, "ppe_setup");
   if (S.nft) {
+    if (L.before) L.before(L.ctx, "ppe_setup");
     if (S.dim == 2) {
       if (S.mixed) k_setup_fluid<2, true><<<S.nft, S.T, 0, L.stream>>>(S);
       else k_setup_fluid<2, false><<<S.nft, S.T, 0, L.stream>>>(S);
@@ -463,8 +463,10 @@ cudaError_t launch_ppe_setup(const State &S, const Launch &L) {
       if (S.mixed) k_setup_fluid<3, true><<<S.nft, S.T, 0, L.stream>>>(S);
       else k_setup_fluid<3, false><<<S.nft, S.T, 0, L.stream>>>(S);
     }
+    if (L.after) L.after(L.ctx, "ppe_setup", double(S.nf), 1);
   }
   if (S.nwt) {
+    if (L.before) L.before(L.ctx, "ppe_setup_wall");
     if (S.dim == 2) {
       if (S.mixed) k_setup_wall<2, true><<<S.nwt, S.T, 0, L.stream>>>(S);
       else k_setup_wall<2, false><<<S.nwt, S.T, 0, L.stream>>>(S);
@@ -472,8 +474,8 @@ cudaError_t launch_ppe_setup(const State &S, const Launch &L) {
       if (S.mixed) k_setup_wall<3, true><<<S.nwt, S.T, 0, L.stream>>>(S);
       else k_setup_wall<3, false><<<S.nwt, S.T, 0, L.stream>>>(S);
     }
+    if (L.after) L.after(L.ctx, "ppe_setup_wall", double(S.nw), 1);
   }
-  if (L.after) L.after(L.ctx, "ppe_setup", double(S.n), (S.nft ? 1 : 0) + (S.nwt ? 1 : 0));
   return cudaGetLastError();
 }
 

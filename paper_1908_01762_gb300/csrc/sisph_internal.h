@@ -20,6 +20,7 @@ namespace sisph {
 constexpr int kCodeShift = 26;                   // neighbour entry = j | code << 26
 constexpr unsigned kIdxMask = (1u << kCodeShift) - 1u;
 constexpr int kMaxParticles = (1 << kCodeShift) - 1;
+constexpr int kMaxCellsPerAxis = (1 << 21) - 1;     // packed rebuild cell: 21 bits per axis
 
 // Error bits of the device status word.
 constexpr int kErrCapacity = 1;   // a neighbour row overflowed its capacity
@@ -44,6 +45,9 @@ struct CaseDev {
   double p_ref0;
   // derived constants
   double cut2;             // (3h)^2, evaluated as (3*h)*(3*h)
+  double skin;             // Verlet skin s: lists hold every j within 3h + s
+  double cut_s2;           // (3h + s)^2
+  double skin_half2;       // (s/2)^2: a larger displacement forces a rebuild
   double eh2;              // eta h^2
   double inv_h, sig_h;     // quintic at h
   double h2, inv_h2, sig_h2;  // quintic at h/2 (no-slip ghost velocity, Eq. vf)
@@ -68,7 +72,7 @@ struct Barrier {
 // Everything a kernel may need, passed by value.  Pointers are device pointers.
 struct State {
   int dim, ncases, mixed, T;
-  int n, nf, nw, cap, wcap;
+  int n, nf, nw, cap, wcap, scap;
   int nft, nwt;
   const CaseDev *cases;
   const Tile *ftiles, *wtiles;
@@ -86,6 +90,8 @@ struct State {
   double *bx[3], *bxn[3], *bu[3], *but[3], *bm, *brho, *bp;
   int *buid;
   double *xs[3], *us[3];   // stage-1 outputs r*, u*
+  double *xref[3], *bxref[3];  // position at the last rebuild of the case
+  long long *cell, *bcell; // cell of the particle at that rebuild (packed)
   double *uw[3], *nrm[3];  // walls: prescribed velocity, unit normal
   double *nstar[3];        // scratch for the raw normals
   // FP32 mirrors (MIXED)
@@ -96,6 +102,14 @@ struct State {
   // neighbour lists (ELL, column-major: entry k of row i at k*n + i)
   unsigned *nbr;
   int *ncnt;
+  unsigned *snbr;          // skin lists, same layout, capacity scap
+  int *sncnt;
+  int *need;               // per case: rebuild at this refresh
+  int *anyneed;            // some case needs a rebuild
+  int *force;              // next refresh rebuilds every case: 1 at the
+                           // current positions, 2 at the stored rebuild ones
+  long long *nreb;         // rebuilds per case; [ncases]: refreshes that rebuilt
+  long long *nbody;        // rebuild groups run inside conditional graph nodes
   // PPE
   void *coef;              // fac_ij per ELL slot (double or float)
   void *prhs;              // RHS_i (active) else 0
@@ -278,11 +292,14 @@ struct Launch {
   void *ctx;
 };
 
-// nbr.cu
-cudaError_t launch_sort(const State &S, const Launch &L, const double *const pos[3], int gather_mode,
-                        bool gather_static);
-cudaError_t launch_build(const State &S, const Launch &L);
-cudaError_t launch_copy_static(const State &S, const Launch &L);
+// nbr.cu: one refresh of the neighbour lists = check, rebuild, finish;
+// mode 0 at the positions x, mode 1 at the stage-1 output r* (committed).
+cudaError_t launch_refresh_check(const State &S, const Launch &L, int mode);
+cudaError_t launch_refresh_rebuild(const State &S, const Launch &L, int mode, bool gather_static,
+                                   bool count_on_device);
+cudaError_t launch_refresh_finish(const State &S, const Launch &L, int mode);
+cudaError_t launch_set_conditional(const State &S, const Launch &L, cudaGraphConditionalHandle h);
+constexpr int kRebuildKernels = 10;   // kernels of launch_refresh_rebuild
 // passes.cu
 cudaError_t launch_density(const State &S, const Launch &L);
 cudaError_t launch_normals(const State &S, const Launch &L);

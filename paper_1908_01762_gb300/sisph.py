@@ -23,7 +23,7 @@ FP64, MIXED = 0, 1
 PREF_FIXED, PREF_TWICE_MAX_FIRST, PREF_EXTERNAL = 0, 1, 2
 FIELDS = {"x": 0, "y": 1, "z": 2, "u": 3, "v": 4, "w": 5, "ut": 6, "vt": 7, "wt": 8, "p": 9,
           "rho": 10, "m": 11, "nx": 12, "ny": 13, "nz": 14, "rhs": 15, "diag": 16,
-          "dx": 17, "dy": 18, "dz": 19}
+          "dx": 17, "dy": 18, "dz": 19, "nskin": 20}
 _NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA",
           ENOTCONVERGED: "ENOTCONVERGED", ENONFINITE: "ENONFINITE", ETIMEOUT: "ETIMEOUT",
           EINTERNAL: "EINTERNAL", ECAPACITY: "ECAPACITY"}
@@ -51,7 +51,8 @@ class sisph_case_params(C.Structure):
 class sisph_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("omega", C.c_double), ("min_iter", C.c_int32),
                 ("eta", C.c_double), ("fs_ratio", C.c_double), ("residual_form", C.c_int32),
-                ("nbr_capacity", C.c_int32), ("block", C.c_int32), ("use_graph", C.c_int32),
+                ("nbr_capacity", C.c_int32), ("skin", C.c_double), ("block", C.c_int32),
+                ("use_graph", C.c_int32),
                 ("barrier_timeout_ms", C.c_double), ("debug_skip_barrier", C.c_int32),
                 ("physics", sisph_case_params)]
 
@@ -59,7 +60,7 @@ class sisph_options(C.Structure):
 class sisph_case_stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("residual", C.c_double),
                 ("lambda_", C.c_double), ("p_ref", C.c_double), ("total_iters", C.c_int64),
-                ("solves", C.c_int64)]
+                ("solves", C.c_int64), ("rebuilds", C.c_int64)]
 
 
 _lib = None

@@ -1,0 +1,141 @@
+"""Verlet skin lists: the neighbour sets stay exact between rebuilds.
+
+Between two cell sorts the lists are filtered out of skin lists (every j
+within 3h + s at the last rebuild); a case is re-sorted only when one of its
+fluid particles moved more than s/2.  These tests run steps, bring the lists
+to the current positions without forcing a rebuild, and compare them with the
+oracle's brute-force/cell lists at exactly the GPU's positions (integer data:
+bit-exact); they check that the rebuild decisions are per case, that the skin
+changes nothing but the summation order, and that moved particles (a caller's
+sisph_set) force a rebuild.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sisph():
+    import paper_1908_01762_gb300 as pkg
+    pkg.build()
+    oracle.build()
+    from paper_1908_01762_gb300 import sisph as mod
+    mod.load_library()
+    return mod
+
+
+def at_gpu_positions(case, sim):
+    c = dict(case)
+    for f in ("x", "y", "z")[:case["dim"]]:
+        c[f] = sim.get(f)
+    return c
+
+
+def assert_lists_exact(sim, case):
+    cg, ig = sim.neighbors()
+    co, io = oracle.neighbors(at_gpu_positions(case, sim))
+    assert np.array_equal(cg, co)
+    assert np.array_equal(ig, io)
+
+
+@pytest.mark.parametrize("name", ["tgv", "db2d", "db3d"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_lists_exact_after_filter_only_refreshes(sisph, name, prec):
+    case = {"tgv": lambda: workloads.taylor_green(40, perturb=0.05, seed=5),
+            "db2d": lambda: workloads.dam_break_2d(dx=0.04),
+            "db3d": lambda: workloads.dam_break_3d(dx=0.05)}[name]()
+    if name == "tgv":
+        # a quarter of the CFL step: the displacement accumulates over
+        # several filter-only refreshes before a rebuild
+        case["params"] = dict(case["params"], dt=case["params"]["dt"] / 4)
+    sim = sisph.Simulation(case, precision=prec)
+    filtered = 0
+    for _ in range(6):
+        sim.step(1)
+        before = sim.stats()[0].rebuilds
+        sim.build_neighbors()
+        after = sim.stats()[0].rebuilds
+        filtered += after == before
+        assert_lists_exact(sim, case)
+    # the filter-only path was exercised at least once
+    assert filtered >= 1
+    sim.close()
+
+
+def test_zero_skin_changes_only_the_summation_order(sisph):
+    case = workloads.dam_break_2d(dx=0.04)
+    # a fixed number of sweeps, so that rounding cannot stop one run a sweep
+    # earlier than the other
+    case["params"] = dict(case["params"], tol=0.0, max_iter=5)
+    a = sisph.Simulation(case)                 # default skin
+    b = sisph.Simulation(case, skin=0.0)       # sort at every refresh
+    a.step(6)
+    b.step(6)
+    assert b.stats()[0].rebuilds == 1 + 2 * 6
+    assert a.stats()[0].rebuilds < b.stats()[0].rebuilds
+    assert a.stats()[0].total_iters == b.stats()[0].total_iters
+    for f in ("x", "y", "u", "v", "p"):
+        ga, gb = a.get(f), b.get(f)
+        scale = max(np.max(np.abs(gb)), 1e-300)
+        assert np.max(np.abs(ga - gb)) / scale < 1e-11, f
+    a.close()
+    b.close()
+
+
+def test_rebuild_decisions_are_per_case(sisph):
+    slow = workloads.taylor_green(30, perturb=0.05, seed=2, U=0.05)
+    fast = workloads.taylor_green(30, perturb=0.05, seed=3, U=1.0)
+    slow["params"] = dict(slow["params"], dt=fast["params"]["dt"])
+    batch = sisph.Simulation([slow, fast])
+    batch.step(8)
+    st = batch.stats()
+    assert st[0].rebuilds < st[1].rebuilds
+    for k, c in enumerate((slow, fast)):
+        solo = sisph.Simulation(c)
+        solo.step(8)
+        assert solo.stats()[0].rebuilds == st[k].rebuilds
+        solo.close()
+    batch.close()
+
+
+def test_set_positions_forces_a_rebuild(sisph):
+    case = workloads.taylor_green(32, perturb=0.05, seed=9)
+    sim = sisph.Simulation(case, precision=sisph.MIXED)
+    sim.step(2)
+    before = sim.stats()[0].rebuilds
+    x = sim.get("x")
+    rng = np.random.Generator(np.random.PCG64(4))
+    pick = rng.choice(case["n"], 40, replace=False)
+    x[pick] = np.mod(x[pick] + rng.uniform(0.1, 0.4, pick.size), 1.0)   # far beyond the skin
+    sim.set("x", x)
+    sim.build_neighbors()
+    assert sim.stats()[0].rebuilds == before + 1
+    assert_lists_exact(sim, case)
+    sim.step(1)
+    sim.build_neighbors()
+    assert_lists_exact(sim, case)
+    sim.close()
+
+
+def test_checkpoint_with_a_pending_rebuild(sisph, tmp_path):
+    case = workloads.lid_driven_cavity(20)
+    a = sisph.Simulation(case, precision=sisph.MIXED)
+    a.step(2)
+    x = a.get("x")
+    fl = np.nonzero(case["kind"] == 0)[0]
+    x[fl[:5]] += 0.02
+    a.set("x", x)                              # rebuild pending at save time
+    path = tmp_path / "ck.bin"
+    sisph.sisph_save(a.h, path)
+    b = sisph.Simulation(case, precision=sisph.MIXED)
+    sisph.sisph_load(b.h, path)
+    a.step(3)
+    b.step(3)
+    for f in ("x", "y", "u", "v", "p"):
+        assert np.array_equal(a.get(f), b.get(f)), f
+    a.close()
+    b.close()
