@@ -114,6 +114,10 @@ typedef struct {
   int32_t use_graph;            /* capture sisph_step in a CUDA graph and replay it */
   double barrier_timeout_ms;    /* budget of one grid-barrier wait */
   int32_t debug_skip_barrier;   /* test hook: block 1 skips its first barrier arrival */
+  int32_t ppe_sync;             /* how sweeps synchronise: 0 auto (default: per-tile
+                                   flags when each block owns at most one fluid and
+                                   one wall tile, else a grid barrier), 1 grid
+                                   barrier after every phase, 2 per-tile flags */
   sisph_case_params physics;    /* case defaults used by sisph_create */
 } sisph_options;
 
@@ -219,13 +223,18 @@ int sisph_set_stream(sisph_t s, void *cuda_stream);
 
 /* Kernel timing with CUDA events on the handle's stream.  on = 0 stops it.
  * With only == NULL every kernel launch is bracketed by events and CUDA
- * graphs are not used (a diagnostic mode).  With only naming one kernel
- * ("ppe_sweeps", "build", "sort", "stage1", ...) only its launches are
- * bracketed, and graph replay stays on: the events are recorded as event
- * nodes of the captured step, so the kernel is timed inside the normal
- * graph-replayed step (the library then waits for each replayed step to read
- * them).  sisph_profile_get returns, for one kernel name, the launch count,
- * the summed device time in ms and the summed work units (particles). */
+ * graphs are not used (a diagnostic mode).  With only naming one site or a
+ * comma-separated list ("ppe_sweeps", "filter,stage1", ...; the sites are
+ * check, sort, build, sync, filter, density, ghost, stage1, stage1_walls,
+ * ppe_setup, ppe_setup_wall, ppe_sweeps, pref, pgrad_gtvf, pgrad, gtvf,
+ * update) only their launches are bracketed, and graph replay stays on: the
+ * events are recorded as event nodes of the captured step, so the kernels
+ * are timed inside the normal graph-replayed step (the library then waits
+ * for each replayed step to read them).  Timing "sort" or "build" takes the
+ * neighbour rebuild group out of its conditional graph node (its kernels
+ * then run every refresh and return at once when no case needs a rebuild).
+ * sisph_profile_get returns, for one site, the launch count, the summed
+ * device time in ms and the summed work units (particles). */
 int sisph_profile_enable(sisph_t s, int32_t on, const char *only);
 int sisph_profile_get(sisph_t s, const char *kernel, int64_t *launches, double *total_ms,
                       double *units);

@@ -67,6 +67,7 @@ struct sisph_s {
   // profiling
   bool profiling = false;
   std::string prof_only;           // empty: every kernel, no graphs
+  std::vector<std::string> prof_set;  // prof_only split at commas
   bool capturing = false;
   std::vector<Pending> gsites;     // event nodes inside the captured graph
   std::vector<Pending> pending;
@@ -104,7 +105,11 @@ cudaError_t dalloc(sisph_t s, T **p, size_t count) {
 }
 
 bool profiled(sisph_t s, const char *name) {
-  return s->profiling && (s->prof_only.empty() || s->prof_only == name);
+  if (!s->profiling) return false;
+  if (s->prof_only.empty()) return true;
+  for (const auto &q : s->prof_set)
+    if (q == name) return true;
+  return false;
 }
 
 void before_cb(void *ctx, const char *name) {
@@ -253,7 +258,7 @@ cudaError_t do_refresh(sisph_t s, int mode, bool first) {
   cudaError_t e = launch_refresh_check(s->S, L, mode);
   if (e != cudaSuccess) return e;
   const bool prof_group =
-      s->profiling && (s->prof_only.empty() || s->prof_only == "sort" || s->prof_only == "build");
+      profiled(s, "sort") || profiled(s, "build");
   if (s->capturing && !prof_group && !s->no_conditional) {
     e = capture_rebuild_conditional(s, mode, first);
   } else if (s->capturing) {
@@ -476,6 +481,7 @@ void sisph_default_options(sisph_options *o) {
   o->use_graph = 1;
   o->barrier_timeout_ms = 2000.0;
   o->debug_skip_barrier = 0;
+  o->ppe_sync = 0;
   sisph_default_case(&o->physics);
 }
 
@@ -498,6 +504,7 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   if (!(opt.omega > 0.0 && opt.omega <= 1.0)) return fail(nullptr, SISPH_EINVAL, "omega must be in (0, 1]");
   if (opt.min_iter < 1) return fail(nullptr, SISPH_EINVAL, "min_iter must be >= 1");
   if (!(opt.skin >= 0.0 && opt.skin <= 1.0)) return fail(nullptr, SISPH_EINVAL, "skin must be in [0, 1]");
+  if (opt.ppe_sync < 0 || opt.ppe_sync > 2) return fail(nullptr, SISPH_EINVAL, "ppe_sync must be 0, 1 or 2");
   const int dim = parts[0].dim;
   if (dim != 2 && dim != 3) return fail(nullptr, SISPH_EINVAL, "dim must be 2 or 3");
   int64_t ntot = 0, nftot = 0;
@@ -548,6 +555,7 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   S.min_iter = opt.min_iter;
   S.residual_form = opt.residual_form;
   S.debug_skip_barrier = opt.debug_skip_barrier;
+  S.ppe_sync = opt.ppe_sync;
 
   // static layout: per case [fluid | walls]; tiles never straddle a block
   std::vector<int> order;  // layout position -> caller index (global)
@@ -575,8 +583,10 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
     D.ftile = int(s->hft.size());
     for (int64_t b = 0; b < nfc; b += T) s->hft.push_back(Tile{int(pos + b), int(pos + std::min<int64_t>(nfc, b + T)), c, 0});
     D.nftile = int(s->hft.size()) - D.ftile;
+    D.wtile = int(s->hwt.size());
     for (int64_t b = 0; b < nwc; b += T)
       s->hwt.push_back(Tile{int(pos + nfc + b), int(pos + nfc + std::min<int64_t>(nwc, b + T)), c, 1});
+    D.nwtile = int(s->hwt.size()) - D.wtile;
     for (int64_t i = 0; i < P.n; ++i) case_of[pos + i] = c;
     for (int64_t i = 0; i < nwc; ++i) wall_at.push_back(int(pos + nfc + i));
     // neighbour capacity from the lattice count of the 3h ball
@@ -670,8 +680,7 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   AR(&S.coef, N * size_t(S.cap));
   AR(&S.prhs, N);
   AR(&S.pwd, N);
-  AR(&S.pb[0], N);
-  AR(&S.pb[1], N);
+  for (int q = 0; q < 4; ++q) AR(&S.pb[q], N);
   A(&S.rhs_out, N);
   A(&S.diag_out, N);
   size_t NW = std::max<size_t>(1, size_t(s->nw));
@@ -680,10 +689,17 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   AR(&S.wcoef, NW * size_t(S.wcap));
   AR(&S.wsinv, NW);
   AR(&S.wh, NW);
-  A(&S.tile_part, 2 * size_t(std::max(1, S.nft)));
+  A(&S.tile_part, 8 * size_t(std::max(1, S.nft)));   // four sweeps in flight
   A(&S.tile_lam, size_t(std::max(1, S.nft)));
   A(&S.act, 2 * size_t(ncases));
-  A(&S.iters, ncases); A(&S.pstat, ncases); A(&S.par, 2 * size_t(ncases));
+  A(&S.iters, ncases); A(&S.pstat, ncases); A(&S.par, 5 * size_t(ncases));
+  A(&S.dsw, ncases);
+  int *dtile_of;
+  A(&dtile_of, N);
+  const size_t NT = size_t(std::max(1, S.nft + S.nwt));
+  A(&S.deps, NT * kDepCap);
+  A(&S.ndeps, NT);
+  A(&S.tflag, NT);
   A(&S.resid, ncases); A(&S.lam, ncases);
   A(&S.iters_tot, ncases); A(&S.solves, ncases);
   A(&S.pref, ncases); A(&S.pref_set, ncases);
@@ -701,6 +717,7 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   S.wtiles = dwt;
   S.case_of = dcase_of;
   S.wall_at = dwall_at;
+  S.tile_of = dtile_of;
 
   e = cudaStreamCreateWithFlags(&s->own_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking);
@@ -778,6 +795,17 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   for (size_t t = 0; t < N; ++t) hi[t] = order[t];
   if (e == cudaSuccess) e = cudaMemcpy(S.uid, hi.data(), N * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(dcase_of, case_of.data(), N * sizeof(int), cudaMemcpyHostToDevice);
+  {
+    std::vector<int> tof(N, 0);
+    for (int b = 0; b < S.nft; ++b)
+      for (int q = s->hft[b].beg; q < s->hft[b].end; ++q) tof[q] = b;
+    for (int b = 0; b < S.nwt; ++b)
+      for (int q = s->hwt[b].beg; q < s->hwt[b].end; ++q) tof[q] = S.nft + b;
+    if (e == cudaSuccess) e = cudaMemcpy(dtile_of, tof.data(), N * sizeof(int), cudaMemcpyHostToDevice);
+    // no lists yet: until a PPE set-up builds them, a tile waits for its whole case
+    std::vector<int> nd(NT, -1);
+    if (e == cudaSuccess) e = cudaMemcpy(S.ndeps, nd.data(), NT * sizeof(int), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess && !wall_at.empty())
     e = cudaMemcpy(dwall_at, wall_at.data(), wall_at.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(dcases, s->hc.data(), ncases * sizeof(CaseDev), cudaMemcpyHostToDevice);
@@ -816,8 +844,11 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, dev);
-  int bps = ppe_max_blocks_per_sm(S, S.T);
+  int bps = ppe_max_blocks_per_sm(S, S.T, false);
   if (bps < 1) bps = 1;
+  int bps2 = ppe_max_blocks_per_sm(S, S.T, true);
+  if (bps2 < 1) bps2 = 1;
+  S.grid_cap_p2p = bps2 * nsm;
   int want = std::max({S.nft, int((s->nw + S.T - 1) / S.T), ncases, 1});
   s->grid = std::min(want, bps * nsm);
   S.barrier_budget = (long long)(opt.barrier_timeout_ms * double(clk > 0 ? clk : 2000000));
@@ -1120,6 +1151,13 @@ int sisph_profile_enable(sisph_t s, int32_t on, const char *only) {
   if (o != s->prof_only || (on != 0) != s->profiling) destroy_graphs(s);  // recapture
   s->profiling = on != 0;
   s->prof_only = o;
+  s->prof_set.clear();
+  for (size_t a = 0; a <= o.size() && !o.empty();) {
+    size_t b = o.find(',', a);
+    if (b == std::string::npos) b = o.size();
+    if (b > a) s->prof_set.push_back(o.substr(a, b - a));
+    a = b + 1;
+  }
   if (on) s->prof.clear();
   return SISPH_OK;
 }

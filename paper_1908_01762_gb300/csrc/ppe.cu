@@ -22,6 +22,52 @@ __device__ __forceinline__ void kahan_add(R &sum, R &comp, R v) {
 }
 
 // ---------------------------------------------------------------------------
+// Tile dependencies of the point-to-point sweeps: the set of other tiles
+// whose rows a tile's PPE rows read, collected in a shared-memory hash set
+// while the rows are set up, then written as a list (ndeps = -1 when the
+// list would exceed kDepCap or the set overflows: the tile then waits for
+// every tile of its case).
+// ---------------------------------------------------------------------------
+constexpr int kHash = 512;
+
+struct DepSet {
+  int *tab;        // kHash slots, -1 empty
+  int *over;       // overflow flag
+  __device__ __forceinline__ void init() {
+    for (int q = threadIdx.x; q < kHash; q += blockDim.x) tab[q] = -1;
+    if (threadIdx.x == 0) *over = 0;
+    __syncthreads();
+  }
+  __device__ __forceinline__ void insert(int key) {
+    unsigned h = (unsigned(key) * 2654435761u) >> 23;
+    for (int probe = 0; probe < kHash; ++probe) {
+      const int cur = tab[h];
+      if (cur == key) return;
+      if (cur == -1) {
+        const int old = atomicCAS(tab + h, -1, key);
+        if (old == -1 || old == key) return;
+      }
+      h = (h + 1) & unsigned(kHash - 1);
+    }
+    *over = 1;
+  }
+  __device__ __forceinline__ void write(const State &S, int b, int *cnt) {
+    __syncthreads();
+    if (threadIdx.x == 0) *cnt = 0;
+    __syncthreads();
+    for (int q = threadIdx.x; q < kHash; q += blockDim.x) {
+      const int key = tab[q];
+      if (key >= 0) {
+        const int pos = atomicAdd(cnt, 1);
+        if (pos < kDepCap) S.deps[(long long)b * kDepCap + pos] = key;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) S.ndeps[b] = (*over || *cnt > kDepCap) ? -1 : *cnt;
+  }
+};
+
+// ---------------------------------------------------------------------------
 // Fluid set-up: RHS_i = sum_j -(m_j/(rho_j dt)) u*_ij . grad_i W_ij and
 // fac_ij = 4 m_j/(rho_i (rho_i+rho_j)) (r_ij . grad_i W_ij)/(r^2 + eta h^2),
 // D_ii = sum_j fac_ij (Kahan-compensated in FP32 for the MIXED form).  A
@@ -34,6 +80,10 @@ __global__ void k_setup_fluid(State S) {
   const Tile &t = S.ftiles[blockIdx.x];
   int i = t.beg + threadIdx.x;
   const CaseDev &P = S.cases[t.c];
+  __shared__ int dtab[kHash];
+  __shared__ int dover, dcnt;
+  DepSet deps{dtab, &dover};
+  deps.init();
   double lam = 0.0;
   if (i < t.end) {
     KC<R> K;
@@ -90,7 +140,13 @@ __global__ void k_setup_fluid(State S) {
           dg += fac;
         }
       }
-      if (valid) coef[(long long)k * _n + i] = fac;
+      if (valid) {
+        coef[(long long)k * _n + i] = fac;
+        if (j != i) {
+          const int dt = S.tile_of[j];
+          if (dt != int(blockIdx.x)) deps.insert(dt);
+        }
+      }
     })
     bool fs = P.free_surface && (double(ri) / P.rho0 < S.fs_ratio);
     bool active = (dg != R(0)) && !fs;
@@ -106,6 +162,7 @@ __global__ void k_setup_fluid(State S) {
     }
     if (active) lam = fabs(double(rhs) / double(dg));
   }
+  deps.write(S, blockIdx.x, &dcnt);
   __shared__ double sh[32];
   for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = lam;
@@ -124,11 +181,8 @@ __global__ void k_setup_fluid(State S) {
 // fluid entries.
 // ---------------------------------------------------------------------------
 template <int DIM, bool MX>
-__global__ void k_setup_wall(State S) {
+__device__ __forceinline__ void wall_row(const State &S, const Tile &t, int i, DepSet &deps) {
   using R = typename std::conditional<MX, float, double>::type;
-  const Tile &t = S.wtiles[blockIdx.x];
-  int i = t.beg + threadIdx.x;
-  if (i >= t.end) return;
   const CaseDev &P = S.cases[t.c];
   KC<R> K;
   K.set(P, P.h, P.inv_h, P.sig_h);
@@ -162,6 +216,7 @@ __global__ void k_setup_wall(State S) {
       rj = S.rho[j];
     }
     R w = K.sig * poly_w<R>(qof<R>(sqrt_r(r2), K.h, K.ih));
+    deps.insert(S.tile_of[j]);
     S.widx[(long long)cnt * nw + r] = j;
     wc[(long long)cnt * nw + r] = w;
     ++cnt;
@@ -174,6 +229,19 @@ __global__ void k_setup_wall(State S) {
   static_cast<R *>(S.wsinv)[r] = sw > R(0) ? R(1) / sw : R(0);
   static_cast<R *>(S.wh)[r] = hw;
 }
+
+template <int DIM, bool MX>
+__global__ void k_setup_wall(State S) {
+  const Tile &t = S.wtiles[blockIdx.x];
+  int i = t.beg + threadIdx.x;
+  __shared__ int dtab[kHash];
+  __shared__ int dover, dcnt;
+  DepSet deps{dtab, &dover};
+  deps.init();
+  if (i < t.end) wall_row<DIM, MX>(S, t, i, deps);
+  deps.write(S, S.nft + blockIdx.x, &dcnt);
+}
+
 
 // ---------------------------------------------------------------------------
 // Grid barrier with a bounded wait.  All blocks are co-resident (cooperative
@@ -249,17 +317,149 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double *sh) {
 }
 
 // ---------------------------------------------------------------------------
-// Persistent damped-Jacobi solve for all cases, one launch.
+// One wall row of Eq. p-shepard: p_w = (sum_f p_f W_wf + H_w) / sum_f W_wf,
+// clamped at 0 in free-surface flows.  Chunks of 8: the index and weight
+// loads go out together, then the 8 pressure gathers.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R wall_pressure(const State &S, const R *pc, int r, int w, int c) {
+  const R *wc = static_cast<const R *>(S.wcoef);
+  const long long nwl = S.nw;
+  R acc = static_cast<const R *>(S.wh)[r];
+  const int cnt = S.wcnt[r];
+  for (int q0 = 0; q0 < cnt; q0 += 8) {
+    int jj[8];
+    R ww[8];
+    _Pragma("unroll") for (int u = 0; u < 8; ++u) {
+      const int q = q0 + u;
+      const long long o = (long long)q * nwl + r;
+      jj[u] = q < cnt ? S.widx[o] : w;
+      ww[u] = q < cnt ? wc[o] : R(0);
+    }
+    R pv[8];
+    _Pragma("unroll") for (int u = 0; u < 8; ++u) pv[u] = pc[jj[u]];
+    _Pragma("unroll") for (int u = 0; u < 8; ++u) acc += ww[u] * pv[u];
+  }
+  R pw = acc * static_cast<const R *>(S.wsinv)[r];
+  if (S.cases[c].free_surface && pw < R(0)) pw = R(0);
+  return pw;
+}
+
+// One fluid row of Eq. p-sor: RHS_i + sum_j fac_ij p^k_j, in chunks of 8
+// slots (8 independent index/coefficient loads, then 8 independent
+// gathers); slots past the row's end read the row itself with a zero
+// coefficient.
+template <typename R>
+__device__ __forceinline__ R jacobi_sum(const State &S, const R *pc, int i, R acc, int cnt) {
+  const R *coef = static_cast<const R *>(S.coef);
+  const long long n = S.n;
+  for (int q0 = 0; q0 < cnt; q0 += 8) {
+    unsigned e[8];
+    R cf[8];
+    _Pragma("unroll") for (int u = 0; u < 8; ++u) {
+      const int q = q0 + u;
+      const long long o = (long long)q * n + i;
+      e[u] = q < cnt ? S.nbr[o] : unsigned(i);
+      cf[u] = q < cnt ? coef[o] : R(0);
+    }
+    R pj[8];
+    _Pragma("unroll") for (int u = 0; u < 8; ++u) pj[u] = pc[e[u] & kIdxMask];
+    _Pragma("unroll") for (int u = 0; u < 8; ++u) acc += cf[u] * pj[u];
+  }
+  return acc;
+}
+
+// Block sums of |p^{k+1} - p^k| and |p^{k+1}| of one tile: in the sweep's
+// precision over the tile's 256 rows, returned in FP64 in thread 0.
+template <bool MX>
+__device__ __forceinline__ void tile_sums(double &dn, double &dp, double *sh,
+                                          typename std::conditional<MX, float, double>::type dnr,
+                                          typename std::conditional<MX, float, double>::type dpr) {
+  if constexpr (MX) {
+    block_sum2f(dnr, dpr, sh);
+    dn = double(dnr);
+    dp = double(dpr);
+  } else {
+    dn = dnr;
+    dp = dpr;
+    block_sum2(dn, dp, sh);
+  }
+}
+
+// Eq. convergence for case c after sweep k, by the block that completed the
+// case's last tile: the tile sums are added in tile order -- thread q adds
+// tiles q, q+T, q+2T, ..., then the block tree -- so the result does not
+// depend on which block arrives last.  At least min_iter sweeps, at most
+// max_iter.  Thread 0 records the decision; *fin_out (thread 0) receives the
+// sweep count at which the case stopped, or 0 if it continues.  The result
+// lives in buffer (sweeps % ring).
+__device__ __forceinline__ int decide_case(const State &S, int c, int k, const double *part, double *sh,
+                                           int ring) {
+  const CaseDev &P = S.cases[c];
+  const int T = blockDim.x;
+  double num = 0.0, den = 0.0, lm = 0.0;
+  for (int q = threadIdx.x; q < P.nftile; q += T) {
+    num += __ldcg(part + 2 * (P.ftile + q));
+    den += __ldcg(part + 2 * (P.ftile + q) + 1);
+    if (k == 0) lm = fmax(lm, __ldcg(S.tile_lam + P.ftile + q));
+  }
+  block_sum2(num, den, sh);
+  if (k == 0) {
+    for (int o = 16; o > 0; o >>= 1) lm = fmax(lm, __shfl_xor_sync(0xffffffffu, lm, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = lm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m = sh[0];
+      for (int w = 1; w < (T >> 5); ++w) m = fmax(m, sh[w]);
+      S.lam[c] = m;
+    }
+  }
+  int stop_at = 0;
+  if (threadIdx.x == 0) {
+    const int kk = k + 1;                    // sweeps completed
+    const double lamc = S.lam[c];
+    double lam = S.residual_form == 1 ? double(P.nf) * lamc : lamc;
+    double dd = lam > den ? lam : den;
+    double res = dd > 0.0 ? num / dd : num;
+    int go = 1, st = 0;
+    if (!isfinite(res)) { go = 0; st = SISPH_ENONFINITE; }
+    else if (kk >= S.min_iter && res < P.tol) go = 0;
+    else if (kk >= P.max_iter) { go = 0; st = SISPH_ENOTCONVERGED; }
+    S.iters[c] = kk;
+    S.resid[c] = res;
+    if (!go) {
+      S.pstat[c] = st;
+      S.par[c] = kk % ring;
+      S.iters_tot[c] += kk;
+      S.solves[c] += 1;
+      if (st == SISPH_ENONFINITE) atomicOr(S.err, kErrNonFinite);
+      if (st == SISPH_ENOTCONVERGED) atomicOr(S.err, kErrNotConv);
+      stop_at = kk;
+    }
+  }
+  return stop_at;
+}
+
+// A case without fluid has nothing to solve; its solve still counts (one
+// block calls this).
+__device__ __forceinline__ void count_empty_solves(const State &S) {
+  if (threadIdx.x == 0)
+    for (int c = 0; c < S.ncases; ++c)
+      if (S.cases[c].nf == 0) S.solves[c] += 1;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent damped-Jacobi solve for all cases, one launch, grid barrier form.
 //   W phase k: every case that swept in F phase k-1 (or k = 0) extrapolates
 //     its wall pressure from p^k (Eq. p-shepard, clamped at 0 for
 //     free-surface flows); for a case that has just finished this is the
 //     final wall update.  Skipped, with its barrier, when no case has walls.
 //   F phase k: for every unfinished case
 //       p^{k+1}_i = omega/D_ii (RHS_i + sum_j fac_ij p^k_j) + (1 - omega) p^k_i
-//     with per-tile FP64 sums of |p^{k+1}-p^k| and |p^{k+1}|.  The block that
-//     completes the last tile of a case (per-case arrival counter) adds that
-//     case's tile sums in tile order -- the same order whoever arrives last --
-//     and applies Eq. convergence: at least min_iter sweeps, at most max_iter.
+//     with per-tile FP64 sums of |p^{k+1}-p^k| and |p^{k+1}|; the block that
+//     completes the last tile of a case (per-case arrival counter) applies
+//     Eq. convergence (decide_case).
 //   grid barrier after each phase.
 // p^k lives in buffer k&1.  Pressures written by other blocks are read with
 // ordinary (L1-cached) loads: every grid barrier ends with an acquire fence
@@ -338,13 +538,10 @@ __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
       const Tile &t = S.ftiles[tt];
       if (__ldcg(done + t.c)) continue;
       int i = t.beg + threadIdx.x;
-      double dn = 0.0, dp = 0.0;
       R dnr = R(0), dpr = R(0);
       if (i < t.end) {
         R acc = prhs[i];
         const int cnt = S.ncnt[i];
-        // chunks of 8 slots: 8 independent index/coefficient loads, then 8
-        // independent gathers, so a row costs a few memory round trips
         for (int q0 = 0; q0 < cnt; q0 += 8) {
           unsigned e[8];
           R cf[8];
@@ -364,17 +561,8 @@ __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
         dnr = fabs(pnew - po);
         dpr = fabs(pnew);
       }
-      // tile sums in the sweep's precision (256 terms), the sum over tiles
-      // and cases in FP64
-      if constexpr (MX) {
-        block_sum2f(dnr, dpr, sh);
-        dn = double(dnr);
-        dp = double(dpr);
-      } else {
-        dn = dnr;
-        dp = dpr;
-        block_sum2(dn, dp, sh);
-      }
+      double dn, dp;
+      tile_sums<MX>(dn, dp, sh, dnr, dpr);
       if (threadIdx.x == 0) {
         S.tile_part[2 * tt] = dn;
         S.tile_part[2 * tt + 1] = dp;
@@ -384,49 +572,15 @@ __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
       }
       __syncthreads();
       if (flag) {
-        // last tile of this case: Eq. convergence over all of its tiles
         __threadfence();
         const int c = t.c;
-        const CaseDev &P = S.cases[c];
-        double num = 0.0, den = 0.0, lm = 0.0;
-        for (int q = threadIdx.x; q < P.nftile; q += T) {
-          num += __ldcg(S.tile_part + 2 * (P.ftile + q));
-          den += __ldcg(S.tile_part + 2 * (P.ftile + q) + 1);
-          if (k == 0) lm = fmax(lm, __ldcg(S.tile_lam + P.ftile + q));
-        }
-        block_sum2(num, den, sh);
-        if (k == 0) {
-          for (int o = 16; o > 0; o >>= 1) lm = fmax(lm, __shfl_xor_sync(0xffffffffu, lm, o));
-          __syncthreads();
-          if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = lm;
-          __syncthreads();
-          if (threadIdx.x == 0) {
-            double m = sh[0];
-            for (int w = 1; w < (T >> 5); ++w) m = fmax(m, sh[w]);
-            S.lam[c] = m;
-          }
-        }
+        const int stop_at = decide_case(S, c, k, S.tile_part, sh, 2);
         if (threadIdx.x == 0) {
-          const int kk = k + 1;                    // sweeps completed
-          const double lamc = S.lam[c];
-          double lam = S.residual_form == 1 ? double(P.nf) * lamc : lamc;
-          double dd = lam > den ? lam : den;
-          double res = dd > 0.0 ? num / dd : num;
-          int go = 1, st = 0;
-          if (!isfinite(res)) { go = 0; st = SISPH_ENONFINITE; }
-          else if (kk >= S.min_iter && res < P.tol) go = 0;
-          else if (kk >= P.max_iter) { go = 0; st = SISPH_ENOTCONVERGED; }
-          S.iters[c] = kk;
-          S.resid[c] = res;
           arrive[c] = 0u;
-          if (!go) {
-            S.pstat[c] = st;
-            S.par[c] = kk & 1;
-            fin[c] = kk;
+          if (stop_at) {
+            fin[c] = stop_at;
             __threadfence();
             done[c] = 1;
-            if (st == SISPH_ENONFINITE) atomicOr(S.err, kErrNonFinite);
-            if (st == SISPH_ENOTCONVERGED) atomicOr(S.err, kErrNotConv);
           }
         }
         __syncthreads();
@@ -445,10 +599,278 @@ __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
     S.p[i] = double(v);
     if constexpr (MX) S.pf[i] = v;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (blockIdx.x == 0) count_empty_solves(S);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent damped-Jacobi solve, point-to-point form: no grid barrier.
+// Every tile (fluid tiles, then wall tiles, numbered 0..nft+nwt) counts its
+// completed phases in a flag.  Phase W(k) of a wall tile needs F(k-1) done
+// in the fluid tiles its rows read; phase F(k) of a fluid tile needs F(k-1)
+// done in its fluid dependencies and W(k) done in its wall dependencies (the
+// lists are built with the PPE rows; a tile whose list overflowed waits for
+// every tile of its case).  Neighbourhoods are symmetric, so neighbouring
+// tiles are never more than one phase apart.
+// p^k lives in buffer k % 4.  The convergence decision after sweep k
+// (decide_case) is awaited with a lag: W(k) and F(k) wait for the decision
+// after sweep k - lag(k) (lag 2 for the first sweeps, 4 after), so tiles run
+// ahead while the decision is being made.  A case that stopped with fin
+// sweeps needs F(k) for k < fin and W(k) for k <= fin (W(fin) is the final
+// wall update); a phase known to be unneeded is skipped, one not yet known
+// runs and writes a buffer other than fin % 4 (the lag never exceeds the
+// ring), so which phases run may depend on timing but the result does not:
+// it equals the grid barrier form's bit for bit.  Needed phases wait only on
+// needed phases; a waiting phase that learns it is unneeded gives up.  A
+// block takes its tiles phase by phase (W tiles, then F tiles, for k = 0,
+// 1, ...); every wait is for an earlier phase, so co-resident blocks always
+// progress.  Waits are bounded: past the budget the kernel raises the
+// timeout flag and every block returns.
+// ---------------------------------------------------------------------------
+constexpr int kRing = 4;
+
+__device__ __forceinline__ int p2p_lag(int k) { return k < 4 ? 2 : kRing; }
+
+__device__ __forceinline__ bool p2p_aborted(const State &S) {
+  return *reinterpret_cast<volatile int *>(&S.bar->err) != 0;
+}
+
+// Whether phase k (wall: W(k), else F(k)) of case c is known to be unneeded.
+__device__ __forceinline__ bool p2p_unneeded(const State &S, int c, int k, bool wall) {
+  if (!*reinterpret_cast<volatile const int *>(S.act + c)) return false;
+  __threadfence();
+  const int fin = __ldcg(S.act + S.ncases + c);
+  return wall ? fin <= k - 1 : fin <= k;
+}
+
+// Wait (one thread) until *f >= need.  1: reached; 0: the phase turned out
+// unneeded; -1: timeout or abort.
+__device__ __forceinline__ int p2p_wait(const State &S, const int *f, int need, int c, int k, bool wall) {
+  volatile const int *vf = f;
+  if (*vf >= need) return 1;
+  const long long t0 = clock64();
+  for (;;) {
+    __nanosleep(32);
+    if (*vf >= need) return 1;
+    if (p2p_unneeded(S, c, k, wall)) return 0;
+    if (p2p_aborted(S)) return -1;
+    if (clock64() - t0 > S.barrier_budget) {
+      atomicExch(&S.bar->err, kErrTimeout);
+      return -1;
+    }
+  }
+}
+
+// Whether phase k of a tile of case c runs: waits for the decision after
+// sweep k - lag(k), then skips the phase if it is known to be unneeded.
+// 1 run, 0 skip, -1 timeout.  Block-uniform.
+__device__ __forceinline__ int p2p_runs(const State &S, int c, int k, bool wall, int *shv) {
+  if (threadIdx.x == 0) {
+    int r = 1;
+    const CaseDev &P = S.cases[c];
+    if (P.nf == 0) {
+      r = (wall && k == 0) ? 1 : 0;             // nothing to solve: W(0) only
+    } else {
+      const int need = k - p2p_lag(k) + 1;       // decisions made
+      if (need > 0) r = p2p_wait(S, S.dsw + c, need, c, k, wall);
+      if (r == 1 && p2p_unneeded(S, c, k, wall)) r = 0;
+      if (r == 1) __threadfence();
+    }
+    *shv = r;
+  }
+  __syncthreads();
+  const int r = *shv;
+  __syncthreads();           // every thread has read it before it is reused
+  return r;
+}
+
+// Wait for the dependencies of tile b before its phase k: fluid tiles must
+// have completed need_f phases, wall tiles need_w.  1 run, 0 skip (the
+// phase turned out unneeded), -1 timeout.  Block-uniform.
+__device__ __forceinline__ int p2p_deps(const State &S, int b, int c, int k, bool wall, int need_f,
+                                        int need_w) {
+  const int nd = S.ndeps[b];
+  int r = 1;
+  if (nd >= 0) {
+    for (int q = threadIdx.x; q < nd && r == 1; q += blockDim.x) {
+      const int d = S.deps[(long long)b * kDepCap + q];
+      r = p2p_wait(S, S.tflag + d, d < S.nft ? need_f : need_w, c, k, wall);
+    }
+  } else {
+    // overflowed list: every tile of the case
+    const CaseDev &P = S.cases[c];
+    const int nt = P.nftile + (wall ? 0 : P.nwtile);
+    for (int q = threadIdx.x; q < nt && r == 1; q += blockDim.x) {
+      const int d = q < P.nftile ? P.ftile + q : S.nft + P.wtile + (q - P.nftile);
+      r = p2p_wait(S, S.tflag + d, d < S.nft ? need_f : need_w, c, k, wall);
+    }
+  }
+  if (r == 1) __threadfence();
+  const int bad = __syncthreads_or(r < 0);
+  const int skip = __syncthreads_or(r == 0);
+  return bad ? -1 : (skip ? 0 : 1);
+}
+
+__device__ __forceinline__ void p2p_signal(const State &S, int b, int value) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    *reinterpret_cast<volatile int *>(S.tflag + b) = value;
+  }
+}
+
+// The decision block (the grid's last block, which owns no tile): for every
+// case in turn it waits until all fluid tiles have added their sums of sweep
+// dsw[c], applies Eq. convergence (decide_case) and publishes the decision.
+// Tiles never wait for it except through the lag.  Returns false on timeout.
+template <bool MX>
+__device__ bool p2p_decide_loop(const State &S, double *sh, int *shv) {
+  const int nc = S.ncases;
+  unsigned *arrive = reinterpret_cast<unsigned *>(S.par + nc);   // [kRing][nc]
+  long long t_last = clock64();
+  for (;;) {
+    bool progress = false, left = false;
     for (int c = 0; c < nc; ++c) {
-      S.iters_tot[c] += S.iters[c];
-      S.solves[c] += 1;
+      const CaseDev &P = S.cases[c];
+      if (P.nf == 0) continue;
+      if (threadIdx.x == 0) {
+        int r = 0;       // 0: case done, 1: not ready, 2: decide sweep k
+        if (!*reinterpret_cast<volatile const int *>(S.act + c)) {
+          const int k = *reinterpret_cast<volatile const int *>(S.dsw + c);
+          const unsigned got = *reinterpret_cast<volatile const unsigned *>(arrive + (k % kRing) * nc + c);
+          r = got >= unsigned(P.nftile) ? 2 : 1;
+        }
+        *shv = r;
+      }
+      __syncthreads();
+      const int r = *shv;
+      __syncthreads();
+      if (r == 0) continue;
+      left = true;
+      if (r == 1) continue;
+      __threadfence();
+      const int k = __ldcg(S.dsw + c);
+      const int cur = k % kRing;
+      const int stop_at = decide_case(S, c, k, S.tile_part + size_t(2) * S.nft * cur, sh, kRing);
+      if (threadIdx.x == 0) {
+        arrive[cur * nc + c] = 0u;
+        if (stop_at) {
+          S.act[nc + c] = stop_at;
+          __threadfence();
+          *reinterpret_cast<volatile int *>(S.act + c) = 1;
+        }
+        __threadfence();
+        *reinterpret_cast<volatile int *>(S.dsw + c) = k + 1;
+      }
+      __syncthreads();
+      progress = true;
+    }
+    if (!left) return true;
+    if (progress) {
+      t_last = clock64();
+      continue;
+    }
+    if (threadIdx.x == 0) {
+      int bad = p2p_aborted(S) ? 1 : 0;
+      if (!bad && clock64() - t_last > S.barrier_budget) {
+        atomicExch(&S.bar->err, kErrTimeout);
+        bad = 1;
+      }
+      *shv = bad;
+      if (!bad) __nanosleep(64);
+    }
+    __syncthreads();
+    const int bad = *shv;
+    __syncthreads();
+    if (bad) return false;
+  }
+}
+
+template <bool MX>
+__global__ void __launch_bounds__(256, MX ? 5 : 4) k_sweeps_p2p(State S) {
+  using R = typename std::conditional<MX, float, double>::type;
+  __shared__ double sh[64];
+  __shared__ int shv;
+  const int nb = gridDim.x - 1;      // tile blocks; the last block decides
+  const int nc = S.ncases;
+  if (int(blockIdx.x) == nb) {
+    if (p2p_decide_loop<MX>(S, sh, &shv)) count_empty_solves(S);
+    return;
+  }
+  const R om1 = R(1.0 - S.omega);
+  const R *prhs = static_cast<const R *>(S.prhs);
+  const R *pwd = static_cast<const R *>(S.pwd);
+  unsigned *arrive = reinterpret_cast<unsigned *>(S.par + nc);   // [kRing][nc]
+  // test hook: block 1 never signals a phase nor adds its sums, so every
+  // wait on it runs out
+  const bool skip = S.debug_skip_barrier && blockIdx.x == 1;
+  bool alive = true;
+  for (int k = 0; alive; ++k) {
+    const int cur = k % kRing;
+    R *pc = static_cast<R *>(S.pb[cur]);
+    R *pn = static_cast<R *>(S.pb[(k + 1) % kRing]);
+    bool ran = false;
+    // ---- W(k) on this block's wall tiles ----
+    for (int wt = blockIdx.x; wt < S.nwt && alive; wt += nb) {
+      const Tile &t = S.wtiles[wt];
+      int run = p2p_runs(S, t.c, k, true, &shv);
+      if (run == 1) run = p2p_deps(S, S.nft + wt, t.c, k, true, k, 0);
+      if (run < 0) { alive = false; break; }
+      if (!run) continue;
+      ran = true;
+      const int w = t.beg + threadIdx.x;
+      if (w < t.end) {
+        const CaseDev &P = S.cases[t.c];
+        const int r = P.wrow + (w - P.wbeg);
+        pc[w] = wall_pressure<R>(S, pc, r, w, t.c);
+      }
+      if (skip) continue;
+      p2p_signal(S, S.nft + wt, k + 1);
+    }
+    // ---- F(k) on this block's fluid tiles ----
+    for (int tt = blockIdx.x; tt < S.nft && alive; tt += nb) {
+      const Tile &t = S.ftiles[tt];
+      int run = p2p_runs(S, t.c, k, false, &shv);
+      if (run == 1) run = p2p_deps(S, tt, t.c, k, false, k, k + 1);
+      if (run < 0) { alive = false; break; }
+      if (!run) continue;
+      ran = true;
+      const int i = t.beg + threadIdx.x;
+      R dnr = R(0), dpr = R(0);
+      if (i < t.end) {
+        R acc = jacobi_sum<R>(S, pc, i, prhs[i], S.ncnt[i]);
+        R po = pc[i];
+        R pnew = pwd[i] * acc + om1 * po;
+        pn[i] = pnew;
+        dnr = fabs(pnew - po);
+        dpr = fabs(pnew);
+      }
+      if (skip) continue;
+      p2p_signal(S, tt, k + 1);
+      double dn, dp;
+      tile_sums<MX>(dn, dp, sh, dnr, dpr);
+      if (threadIdx.x == 0) {
+        double *part = S.tile_part + size_t(2) * S.nft * cur;
+        part[2 * tt] = dn;
+        part[2 * tt + 1] = dp;
+        __threadfence();
+        atomicAdd(arrive + cur * nc + t.c, 1u);
+      }
+    }
+    if (!ran) break;
+  }
+  if (!alive) return;
+  // ---- publish the final pressure of the tiles this block owns (the same
+  // fluid and wall tiles as in the phases above: their last writes to the
+  // final buffer were this block's own) ----
+  for (int kind = 0; kind < 2; ++kind) {
+    const int ntk = kind ? S.nwt : S.nft;
+    for (int b = blockIdx.x; b < ntk; b += nb) {
+      const Tile &t = kind ? S.wtiles[b] : S.ftiles[b];
+      const int i = t.beg + threadIdx.x;
+      if (i >= t.end) continue;
+      const R v = __ldcg(static_cast<const R *>(S.pb[__ldcg(S.par + t.c)]) + i);
+      S.p[i] = double(v);
+      if constexpr (MX) S.pf[i] = v;
     }
   }
 }
@@ -479,20 +901,37 @@ cudaError_t launch_ppe_setup(const State &S, const Launch &L) {
   return cudaGetLastError();
 }
 
-int ppe_max_blocks_per_sm(const State &S, int block) {
+int ppe_max_blocks_per_sm(const State &S, int block, bool p2p) {
   int nb = 0;
-  if (S.mixed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweeps<true>, block, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweeps<false>, block, 0);
+  if (p2p) {
+    if (S.mixed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweeps_p2p<true>, block, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweeps_p2p<false>, block, 0);
+  } else {
+    if (S.mixed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweeps<true>, block, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweeps<false>, block, 0);
+  }
   return nb;
 }
 
 cudaError_t launch_ppe_sweeps(const State &S, const Launch &L, int grid) {
+  const size_t nc = size_t(S.ncases);
   cudaMemsetAsync(S.bar, 0, sizeof(Barrier), L.stream);
-  // done[nc], fin[nc] = 0; par[nc] and the arrival counters par[nc..2nc) = 0
-  cudaMemsetAsync(S.act, 0, 2 * sizeof(int) * size_t(S.ncases), L.stream);
-  cudaMemsetAsync(S.par, 0, 2 * sizeof(int) * size_t(S.ncases), L.stream);
-  cudaMemsetAsync(S.iters, 0, sizeof(int) * size_t(S.ncases), L.stream);
-  cudaMemsetAsync(S.pstat, 0, sizeof(int) * size_t(S.ncases), L.stream);
+  // done[nc], fin[nc]; par[nc] and the arrival counters par[nc..3nc)
+  cudaMemsetAsync(S.act, 0, 2 * sizeof(int) * nc, L.stream);
+  cudaMemsetAsync(S.par, 0, (1 + kRing) * sizeof(int) * nc, L.stream);
+  cudaMemsetAsync(S.iters, 0, sizeof(int) * nc, L.stream);
+  cudaMemsetAsync(S.pstat, 0, sizeof(int) * nc, L.stream);
+  // point-to-point form when every block can own at most one fluid and one
+  // wall tile (its per-tile waits would otherwise add up), unless forced; it
+  // takes one more block, which makes the convergence decisions
+  const int tiles = S.nft > S.nwt ? S.nft : S.nwt;
+  const bool p2p = S.ppe_sync == 2 || (S.ppe_sync == 0 && S.grid_cap_p2p >= tiles + 1);
+  if (p2p) grid = (tiles + 1 < S.grid_cap_p2p ? tiles + 1 : S.grid_cap_p2p);
+  if (p2p && grid < 2) grid = 2;
+  if (p2p) {
+    cudaMemsetAsync(S.dsw, 0, sizeof(int) * nc, L.stream);
+    cudaMemsetAsync(S.tflag, 0, sizeof(int) * size_t(S.nft + S.nwt > 0 ? S.nft + S.nwt : 1), L.stream);
+  }
   if (L.before) L.before(L.ctx, "ppe_sweeps");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -505,8 +944,13 @@ cudaError_t launch_ppe_sweeps(const State &S, const Launch &L, int grid) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaError_t e;
-  if (S.mixed) e = cudaLaunchKernelEx(&cfg, k_sweeps<true>, S);
-  else e = cudaLaunchKernelEx(&cfg, k_sweeps<false>, S);
+  if (p2p) {
+    if (S.mixed) e = cudaLaunchKernelEx(&cfg, k_sweeps_p2p<true>, S);
+    else e = cudaLaunchKernelEx(&cfg, k_sweeps_p2p<false>, S);
+  } else {
+    if (S.mixed) e = cudaLaunchKernelEx(&cfg, k_sweeps<true>, S);
+    else e = cudaLaunchKernelEx(&cfg, k_sweeps<false>, S);
+  }
   if (L.after) L.after(L.ctx, "ppe_sweeps", 0.0, 1);
   return e;
 }

@@ -21,6 +21,7 @@ constexpr int kCodeShift = 26;                   // neighbour entry = j | code <
 constexpr unsigned kIdxMask = (1u << kCodeShift) - 1u;
 constexpr int kMaxParticles = (1 << kCodeShift) - 1;
 constexpr int kMaxCellsPerAxis = (1 << 21) - 1;     // packed rebuild cell: 21 bits per axis
+constexpr int kDepCap = 96;                         // dependency list of a tile
 
 // Error bits of the device status word.
 constexpr int kErrCapacity = 1;   // a neighbour row overflowed its capacity
@@ -56,6 +57,7 @@ struct CaseDev {
   int fbeg, nf, wbeg, nw;
   int wrow;                // first row of this case in the wall tables
   int ftile, nftile;       // first fluid tile, count
+  int wtile, nwtile;       // first wall tile (in wall-tile numbering), count
 };
 
 struct Tile {
@@ -114,7 +116,8 @@ struct State {
   void *coef;              // fac_ij per ELL slot (double or float)
   void *prhs;              // RHS_i (active) else 0
   void *pwd;               // omega / D_ii (active) else 0
-  void *pb[2];             // pressure ping-pong buffers
+  void *pb[4];             // pressure buffers: p^k in pb[k % 2] (grid barrier
+                           // form) or pb[k % 4] (point-to-point form)
   double *rhs_out, *diag_out;
   int *wcnt;               // wall Shepard rows (fluid neighbours only)
   int *widx;
@@ -130,6 +133,13 @@ struct State {
   int *pref_set;
   Barrier *bar;
   int *err;
+  // point-to-point PPE sweeps (tiles numbered: fluid tiles, then wall tiles)
+  int ppe_sync;            // 0 auto, 1 grid barrier per phase, 2 per-tile flags
+  int grid_cap_p2p;        // co-resident blocks of the point-to-point form
+  const int *tile_of;      // sorted index -> tile
+  int *deps, *ndeps;       // per tile: tiles its PPE rows read (kDepCap each)
+  int *tflag;              // per tile: phases completed in this solve
+  int *dsw;                // per case: convergence decisions made in this solve
   // GTVF
   double *dg[2][3];        // FP64 displacement ping-pong
   float4 *dgf[2];          // FP32 displacement ping-pong
@@ -318,6 +328,6 @@ cudaError_t launch_refresh_mirrors(const State &S, const Launch &L);
 // ppe.cu
 cudaError_t launch_ppe_setup(const State &S, const Launch &L);
 cudaError_t launch_ppe_sweeps(const State &S, const Launch &L, int grid);
-int ppe_max_blocks_per_sm(const State &S, int block);
+int ppe_max_blocks_per_sm(const State &S, int block, bool p2p);
 
 }  // namespace sisph

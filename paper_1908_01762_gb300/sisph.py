@@ -54,6 +54,7 @@ class sisph_options(C.Structure):
                 ("nbr_capacity", C.c_int32), ("skin", C.c_double), ("block", C.c_int32),
                 ("use_graph", C.c_int32),
                 ("barrier_timeout_ms", C.c_double), ("debug_skip_barrier", C.c_int32),
+                ("ppe_sync", C.c_int32),
                 ("physics", sisph_case_params)]
 
 

@@ -44,9 +44,12 @@ def test_non_finite_input_is_reported(sisph):
     sim.close()
 
 
-def test_barrier_timeout_returns_status_and_device_recovers(sisph):
+@pytest.mark.parametrize("sync", [1, 2])
+def test_barrier_timeout_returns_status_and_device_recovers(sisph, sync):
+    """Block 1 never signals its first phase (grid barrier form: never arrives
+    at the first barrier); every wait runs out after 5 ms."""
     case = workloads.taylor_green(40)
-    sim = sisph.Simulation(case, debug_skip_barrier=1, barrier_timeout_ms=5.0)
+    sim = sisph.Simulation(case, debug_skip_barrier=1, barrier_timeout_ms=5.0, ppe_sync=sync)
     sim.density()
     with pytest.raises(sisph.SisphError) as ei:
         sim.ppe_solve(1e-4, 50)

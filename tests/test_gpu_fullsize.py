@@ -91,3 +91,22 @@ def test_fullsize_mixed_decay_rate(sisph, c2):
     assert abs(bg - bo) < 1e-4 * abs(bo)
     assert abs(bo + 8 * math.pi ** 2 / 100) < 0.05 * 8 * math.pi ** 2 / 100
     sim.close()
+
+
+def test_sweep_sync_forms_agree_on_the_batch(sisph):
+    """The batch of 64 cases (about 2.5M particles) has more tiles than the
+    persistent kernel has blocks, so blocks own several tiles of different
+    cases: the point-to-point sweeps must reproduce the grid-barrier form bit
+    for bit, sweep counts included."""
+    cases = workloads.batch_ensemble(64)
+    out = []
+    for sync in (2, 1):
+        sim = sisph.Simulation(cases, precision=sisph.MIXED, ppe_sync=sync)
+        sim.step(2)
+        out.append(({f: sim.get(f) for f in ("x", "y", "u", "v", "p")},
+                    [s.total_iters for s in sim.stats()]))
+        sim.close()
+    (a, ia), (b, ib) = out
+    assert ia == ib
+    for f in a:
+        assert np.array_equal(a[f], b[f]), f

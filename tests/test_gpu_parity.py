@@ -276,6 +276,40 @@ def test_batch_member_equals_solo(sisph, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name", ["db2d", "ldc", "tgv_perturbed", "db3d"])
+def test_sweep_sync_forms_agree(sisph, prec, name):
+    """Point-to-point sweeps (per-tile flags, decisions one sweep behind) and
+    the grid-barrier form give the same pressures and sweep counts."""
+    case = CASES[name]
+    out = []
+    for sync in (2, 1):
+        sim = sisph.Simulation(case, precision=prec, ppe_sync=sync)
+        sim.step(4)
+        out.append(({f: sim.get(f) for f in ("x", "y", "u", "v", "p")}, sim.stats()[0].total_iters))
+        sim.close()
+    (a, ia), (b, ib) = out
+    assert ia == ib
+    for f in a:
+        assert np.array_equal(a[f], b[f]), f
+
+
+def test_sweep_sync_forms_agree_with_an_empty_case(sisph):
+    tank = workloads.still_tank_2d(6, 6, dx=0.1)
+    walls = {k: (v[tank["kind"] == 1] if isinstance(v, np.ndarray) and v.shape == (tank["n"],) else v)
+             for k, v in tank.items()}
+    walls["n"] = int(np.sum(tank["kind"] == 1))
+    cases = [workloads.taylor_green(20, tol=1e-2), walls, workloads.dam_break_2d(dx=0.05)]
+    res = []
+    for sync in (2, 1):
+        sim = sisph.Simulation(cases, ppe_sync=sync)
+        sim.step(3)
+        res.append((sim.get("p"), [(s.iters, s.solves) for s in sim.stats()]))
+        sim.close()
+    assert np.array_equal(res[0][0], res[1][0])
+    assert res[0][1] == res[1][1]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 def test_graph_replay_equals_direct(sisph, prec):
     case = workloads.lid_driven_cavity(24)
     a = sisph.Simulation(case, precision=prec, use_graph=1)
