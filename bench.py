@@ -272,7 +272,7 @@ def run_ours(args, rank, world):
         modeled = [k for k in sites if k == "ppe_sweeps" or kernel_bytes(k, mixed, dim, 1, 1, 1, 1, 1)]
         roof_site = max(modeled, key=lambda k: sites[k]["ms_per_step"])
 
-    sim = sisph.Simulation(cases, precision=prec, use_graph=1)
+    sim = sisph.Simulation(cases, precision=prec, use_graph=0 if args.no_graph else 1)
     sisph.sisph_set_stream(sim.h, stream.cuda_stream)
     n = sim.n
     kinds = np.concatenate([c["kind"] for c in cases])
@@ -357,7 +357,8 @@ def run_ours(args, rank, world):
         "config": {"workload": desc, "n_particles": n, "n_fluid": n_fluid,
                    "cases": len(cases), "precision": args.precision,
                    "ppe_sweeps_per_step": iters_per_step, "l2": "flushed between steps (256 MiB write)",
-                   "graph": "CUDA graph replay per step", "parallelism": f"replicas{world}",
+                   "graph": "direct launches" if args.no_graph else "CUDA graph replay per step",
+                   "parallelism": f"replicas{world}",
                    "neighbour_rebuilds_per_refresh": float(np.mean(rebuilds)) / (2 * args.steps)},
         "ppe_interactions_per_s": world * pairs / (t_ms * 1e-3),
         "roofline": {"kernel": roof_site, "bound": "hbm",
@@ -525,6 +526,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="direct launches instead of the captured step (kernel profilers cannot "
+                         "look inside a graph with conditional nodes)")
     ap.add_argument("--roofline-kernel", default=None, choices=sorted(SITES),
                     help="time this site live instead of the dominant one (skips the site table)")
     ap.add_argument("--study", choices=["tolerance"], default=None,

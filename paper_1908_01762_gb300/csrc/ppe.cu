@@ -441,6 +441,57 @@ __device__ __forceinline__ int decide_case(const State &S, int c, int k, const d
   return stop_at;
 }
 
+// Exclusive prefix over the cases of a per-case count, in shared memory
+// (pre[0..nc], pre[nc] = total); thread t handles a contiguous run of
+// cases.  Returns the total.  Used to spread the work of the cases still
+// iterating evenly over the blocks.
+template <typename F>
+__device__ __forceinline__ int case_prefix(int nc, int *pre, int *wsum, F count) {
+  const int T = blockDim.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = T >> 5;
+  const int per = (nc + T - 1) / T;
+  const int c0 = threadIdx.x * per;
+  int sum = 0;
+  for (int c = c0; c < c0 + per && c < nc; ++c) sum += count(c);
+  int x = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int a = 0;
+    for (int q = 0; q < nw; ++q) {
+      const int t = wsum[q];
+      wsum[q] = a;
+      a += t;
+    }
+    wsum[nw] = a;
+  }
+  __syncthreads();
+  int ex = wsum[w] + x - sum;
+  for (int c = c0; c < c0 + per && c < nc; ++c) {
+    pre[c] = ex;
+    ex += count(c);
+  }
+  if (threadIdx.x == 0) pre[nc] = wsum[nw];
+  __syncthreads();
+  const int total = pre[nc];
+  __syncthreads();
+  return total;
+}
+
+// The case c with pre[c] <= a < pre[c + 1] (pre non-decreasing).
+__device__ __forceinline__ int case_of_index(const int *pre, int nc, int a) {
+  int lo = 0, hi = nc - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= a) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // A case without fluid has nothing to solve; its solve still counts (one
 // block calls this).
 __device__ __forceinline__ void count_empty_solves(const State &S) {
@@ -467,11 +518,18 @@ __device__ __forceinline__ void count_empty_solves(const State &S) {
 // those reads after the other blocks' writes.  Flags and partial sums are
 // read with ld.global.cg.
 // ---------------------------------------------------------------------------
+// Up to this many cases the work of the cases still iterating is spread
+// evenly over the blocks in every phase; beyond, blocks stride over all
+// tiles and skip the finished ones.
+constexpr int kBalCases = 1024;
+
 template <bool MX>
 __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
   using R = typename std::conditional<MX, float, double>::type;
   __shared__ double sh[64];
   __shared__ int flag;
+  __shared__ int apre[kBalCases + 1];
+  __shared__ int wsum[33];
   const unsigned nb = gridDim.x;
   const int T = blockDim.x;
   const int nc = S.ncases;
@@ -497,10 +555,22 @@ __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
     R *pc = static_cast<R *>(S.pb[cur]);
     // ---- W phase: wall extrapolation from p^k ----
     if (S.nw > 0) {
-      for (int r = blockIdx.x * T + threadIdx.x; r < S.nw; r += nb * T) {
+      // wall rows of the cases that take this phase, spread over the grid
+      const bool bal = nc <= kBalCases;
+      // (a case takes W phase k unless it stopped with fin < k sweeps)
+      const int nrows = bal ? case_prefix(nc, apre, wsum, [&](int c) {
+        const int f = __ldcg(fin + c);
+        return (k == 0 || f == 0 || f == k) ? S.cases[c].nw : 0;
+      }) : S.nw;
+      for (int a = blockIdx.x * T + threadIdx.x; a < nrows; a += nb * T) {
+        int r = a;
+        if (bal) {
+          const int c = case_of_index(apre, nc, a);
+          r = S.cases[c].wrow + (a - apre[c]);
+        }
         int w = S.wall_at[r];
         int c = S.case_of[w];
-        if (k > 0 && __ldcg(done + c) && __ldcg(fin + c) != k) continue;
+        if (!bal && k > 0 && __ldcg(done + c) && __ldcg(fin + c) != k) continue;
         R acc = wh[r];
         const int cnt = S.wcnt[r];
         for (int q0 = 0; q0 < cnt; q0 += 8) {
@@ -534,9 +604,23 @@ __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
     }
     // ---- F phase: one damped-Jacobi sweep of the unfinished cases ----
     R *pn = static_cast<R *>(S.pb[cur ^ 1]);
-    for (int tt = blockIdx.x; tt < S.nft; tt += nb) {
+    // fluid tiles of the unfinished cases, spread over the grid.  A case is
+    // counted by its stop count alone, which is 0 until it stops and then
+    // k + 1 if it stops in this very phase: every block, whenever it looks,
+    // counts the same cases.
+    const bool bal = nc <= kBalCases;
+    const int ntiles = bal ? case_prefix(nc, apre, wsum, [&](int c) {
+      const int f = __ldcg(fin + c);
+      return (f == 0 || f > k) ? S.cases[c].nftile : 0;
+    }) : S.nft;
+    for (int a = blockIdx.x; a < ntiles; a += nb) {
+      int tt = a;
+      if (bal) {
+        const int c = case_of_index(apre, nc, a);
+        tt = S.cases[c].ftile + (a - apre[c]);
+      }
       const Tile &t = S.ftiles[tt];
-      if (__ldcg(done + t.c)) continue;
+      if (!bal && __ldcg(done + t.c)) continue;
       int i = t.beg + threadIdx.x;
       R dnr = R(0), dpr = R(0);
       if (i < t.end) {
