@@ -68,7 +68,7 @@ SITES = {"check": "nbr.cu", "sort": "nbr.cu", "build": "nbr.cu", "sync": "nbr.cu
          "stage1": "passes.cu", "stage1_walls": "passes.cu", "ppe_setup": "ppe.cu",
          "ppe_setup_wall": "ppe.cu", "ppe_sweeps": "ppe.cu", "pref": "passes.cu",
          "pgrad_gtvf": "passes.cu", "pgrad": "passes.cu", "gtvf": "passes.cu",
-         "update": "passes.cu"}
+         "update": "passes.cu", "speed_max": "passes.cu", "adapt_dt": "passes.cu"}
 
 
 def measured_traffic(workload, site):

@@ -94,6 +94,9 @@ typedef struct {
   double p_ref;
   double gtvf_hfac;             /* h~ = gtvf_hfac * h (1 internal, 0.5 external flows) */
   int32_t gtvf_K;               /* GTVF sub-steps per time step */
+  int32_t adaptive_dt;          /* 1: the next step's dt from max|u^n| and max|f^n|
+                                   (Sec. 3.2): min(0.25 h/max|u|, 0.25 sqrt(h/max|f|),
+                                   0.25 h^2/nu); dt is then the first step's */
 } sisph_case_params;
 
 /* Solver-wide options.  Defaults from sisph_default_options(). */
@@ -131,6 +134,8 @@ typedef struct {
   int64_t total_iters;          /* sweeps summed over every solve so far */
   int64_t solves;               /* PPE solves so far */
   int64_t rebuilds;             /* cell sorts + skin-list rebuilds so far */
+  double dt;                    /* time step of the next step */
+  double time;                  /* simulated time so far */
 } sisph_case_stats;
 
 /* Field identifiers for sisph_get / sisph_set. */
@@ -227,7 +232,7 @@ int sisph_set_stream(sisph_t s, void *cuda_stream);
  * comma-separated list ("ppe_sweeps", "filter,stage1", ...; the sites are
  * check, sort, build, sync, filter, density, ghost, stage1, stage1_walls,
  * ppe_setup, ppe_setup_wall, ppe_sweeps, pref, pgrad_gtvf, pgrad, gtvf,
- * update) only their launches are bracketed, and graph replay stays on: the
+ * update, speed_max, adapt_dt) only their launches are bracketed, and graph replay stays on: the
  * events are recorded as event nodes of the captured step, so the kernels
  * are timed inside the normal graph-replayed step (the library then waits
  * for each replayed step to read them).  Timing "sort" or "build" takes the

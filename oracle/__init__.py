@@ -43,12 +43,14 @@ class Params(C.Structure):
         ("pgrad_symm", C.c_int32), ("free_surface", C.c_int32), ("ustar_slip", C.c_int32),
         ("pref_mode", C.c_int32), ("p_ref", C.c_double), ("gtvf_hfac", C.c_double),
         ("gtvf_K", C.c_int32), ("residual_form", C.c_int32), ("brute_neighbors", C.c_int32),
+        ("adaptive_dt", C.c_int32),
     ]
 
 
 class Diag(C.Structure):
     _fields_ = [("iters", C.c_int32), ("residual", C.c_double), ("lambda_", C.c_double),
-                ("converged", C.c_int32), ("nonfinite", C.c_int32), ("umax", C.c_double)]
+                ("converged", C.c_int32), ("nonfinite", C.c_int32), ("umax", C.c_double),
+                ("dt", C.c_double)]
 
 
 def lib():
@@ -90,6 +92,8 @@ def lib():
         L.or_ppe_solve.restype = C.c_int32
         L.or_get_pref.argtypes = [C.c_void_p]
         L.or_get_pref.restype = C.c_double
+        L.or_get_dt.argtypes = [C.c_void_p]
+        L.or_get_dt.restype = C.c_double
         L.or_plant_mistake.argtypes = [C.c_int32]
     return _lib
 
@@ -134,7 +138,7 @@ def make_params(case, **over) -> Params:
     for key in ("eta", "omega", "fs_ratio"):
         if key in prm:
             setattr(P, key, float(prm[key]))
-    for key in ("min_iter", "residual_form", "brute_neighbors"):
+    for key in ("min_iter", "residual_form", "brute_neighbors", "adaptive_dt"):
         if key in prm:
             setattr(P, key, int(prm[key]))
     return P
@@ -261,6 +265,11 @@ class Sim:
         ds = (Diag * max(1, nsteps))()
         rc = lib().or_step(self.h, int(nsteps), ds)
         return rc, [ds[i] for i in range(nsteps)]
+
+    @property
+    def dt(self):
+        """Time step of the next step."""
+        return lib().or_get_dt(self.h)
 
     @property
     def p_ref(self):

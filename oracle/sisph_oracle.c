@@ -42,6 +42,7 @@ struct or_sim {
   double lambda;
   int32_t pref_set;
   double p_ref;
+  double fmax;                   /* max_i |f_i| over fluid of the last pressure gradient */
   or_diag last;
 };
 
@@ -365,6 +366,7 @@ int32_t or_set(or_sim *s, const char *field, const double *in) {
 }
 
 double or_get_pref(const or_sim *s) { return s->p_ref; }
+double or_get_dt(const or_sim *s) { return s->prm.dt; }
 
 int64_t or_build_neighbors(or_sim *s) {
   or_csr c = {s->nstart, s->nidx, s->ncap};
@@ -760,6 +762,7 @@ int64_t or_ppe_export(const or_sim *s, double *diag, double *rhs, int32_t *activ
  * ------------------------------------------------------------------------- */
 void or_pressure_gradient(or_sim *s) {
   const or_params *P = &s->prm;
+  s->fmax = 0.0;
   for (int64_t i = 0; i < s->n; ++i) {
     if (s->kind[i] != FLUID) continue;
     double fi[3] = {0, 0, 0};
@@ -775,6 +778,12 @@ void or_pressure_gradient(or_sim *s) {
       else c = -mj / (ri * rj) * ((g_plant == 6) ? (pi - pj) : (pj - pi));
       for (int k = 0; k < 3; ++k) fi[k] += c * g[k];
     }
+    // total acceleration of this step, f_p + (f_visc + f_avisc + f_astress
+    // + f_body) from stage 1 (still in f), for the adaptive time step
+    double ft[3] = {0, 0, 0};
+    for (int k = 0; k < P->dim; ++k) ft[k] = s->f[k][i] + fi[k];
+    double fm = sqrt(or_dot(ft, ft));
+    if (fm > s->fmax) s->fmax = fm;
     for (int k = 0; k < P->dim; ++k) {
       s->f[k][i] = fi[k];
       s->u[k][i] = s->u[k][i] + P->dt * fi[k];
@@ -875,9 +884,35 @@ int32_t or_ppe_solve(or_sim *s, double tol, int32_t max_iter, or_diag *d) {
 
 /* One time step of Algorithm 1 (two neighbour builds: at r^n for stage 1 and
  * at r* for stage 2, as in the two stages of Listing 1). */
+/* ---------------------------------------------------------------------------
+ * Adaptive time step (Sec. 3.2): from the maximum fluid speed max|u^n| at
+ * the start of step n and the maximum total acceleration max|f^n| of that
+ * step (pressure gradient + viscous + body + artificial viscosity and
+ * stress),
+ *   dt^{n+1} = min(0.25 h / max|u^n|, 0.25 sqrt(h / max|f^n|), 0.25 h^2 / nu),
+ * with h_ij = h.  Reading: the viscous limit of the fixed rule stays in the
+ * minimum (the text notes it is constant, not that it is dropped).  A limit
+ * whose denominator is zero is left out; if all are, dt is kept.
+ * ------------------------------------------------------------------------- */
+static double or_next_dt(const or_params *P, double umax, double fmax) {
+  double dt = INFINITY;
+  if (umax > 0.0) dt = fmin(dt, 0.25 * P->h / umax);
+  if (fmax > 0.0) dt = fmin(dt, 0.25 * sqrt(P->h / fmax));
+  if (P->nu > 0.0) dt = fmin(dt, 0.25 * P->h * P->h / P->nu);
+  return isfinite(dt) ? dt : P->dt;
+}
+
 int32_t or_step(or_sim *s, int32_t nsteps, or_diag *d) {
   int32_t rc = 0;
   for (int32_t it = 0; it < nsteps; ++it) {
+    double umax = 0.0;
+    for (int64_t i = 0; i < s->n; ++i) {
+      if (s->kind[i] != FLUID) continue;
+      double ui[3] = {s->u[0][i], s->u[1][i], s->u[2][i]};
+      double um = sqrt(or_dot(ui, ui));
+      if (um > umax) umax = um;
+    }
+    const double dt_used = s->prm.dt;
     if (or_build_neighbors(s) < 0) return -2;
     or_density(s);
     or_ghost_velocity(s, 0);
@@ -900,8 +935,10 @@ int32_t or_step(or_sim *s, int32_t nsteps, or_diag *d) {
     or_gtvf(s);
     or_update(s);
     dd.umax = s->last.umax;
+    dd.dt = dt_used;
     s->last = dd;
     if (d) d[it] = dd;
+    if (s->prm.adaptive_dt) s->prm.dt = or_next_dt(&s->prm, umax, s->fmax);
     if (dd.nonfinite) return -5;
     if (!dd.converged) rc = -4;
   }

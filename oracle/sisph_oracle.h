@@ -42,6 +42,7 @@ typedef struct {
   int32_t gtvf_K;           /* GTVF sub-steps */
   int32_t residual_form;    /* 0: max(Lambda, sum|p|), 1: max(N_F Lambda, sum|p|) */
   int32_t brute_neighbors;  /* 1: O(N^2) search, 0: cell list */
+  int32_t adaptive_dt;      /* 1: next dt from max|u^n| and max|f^n| (Sec. 3.2) */
 } or_params;
 
 typedef struct {
@@ -51,6 +52,7 @@ typedef struct {
   int32_t converged;
   int32_t nonfinite;
   double umax;
+  double dt;                /* time step this step advanced by */
 } or_diag;
 
 void or_default_params(or_params *prm);
@@ -97,6 +99,8 @@ int32_t or_step(or_sim *s, int32_t nsteps, or_diag *d);
 /* PPE alone on the current state (positions, u* in u, rho, p). */
 int32_t or_ppe_solve(or_sim *s, double tol, int32_t max_iter, or_diag *d);
 double or_get_pref(const or_sim *s);
+/* Time step of the next step (changes with the adaptive rule). */
+double or_get_dt(const or_sim *s);
 /* Test hook: plant a known mistake (0 = none) so a test can show a pin fails. */
 void or_plant_mistake(int32_t which);
 

@@ -59,6 +59,7 @@ struct sisph_s {
   int64_t n = 0, nf = 0, nw = 0;
   int kmax = 1;
   int grid = 1;
+  bool adaptive = false;           // some case adapts its time step
   // the captured step
   cudaGraphExec_t gexec = nullptr;
   bool graph_failed = false;
@@ -292,6 +293,7 @@ cudaError_t do_ppe(sisph_t s) {
 cudaError_t do_step(sisph_t s) {
   Launch L = mk_launch(s);
   cudaError_t e = do_refresh(s, 0, false);            // neighbours at r^n
+  if (e == cudaSuccess && s->adaptive) e = launch_speed_max(s->S, L, 0);  // max|u^n| (Sec. 3.2)
   if (e == cudaSuccess) e = launch_density(s->S, L);  // rho (Eq. summation_density)
   if (e == cudaSuccess) e = launch_ghost(s->S, L, 0); // no-slip ghost velocity
   if (e == cudaSuccess) e = launch_stage1(s->S, L);   // u*, r* (Eqs. int:vint, int:rnp1)
@@ -304,11 +306,14 @@ cudaError_t do_step(sisph_t s) {
     if (e == cudaSuccess) e = launch_pgrad_gtvf1(s->S, L);
     if (e == cudaSuccess && s->kmax > 1) e = launch_gtvf(s->S, L, s->kmax, 1);
     if (e == cudaSuccess && s->kmax > 1) e = launch_update(s->S, L, 1);
-    return e;
+  } else {
+    if (e == cudaSuccess) e = launch_pgrad(s->S, L);    // Eq. int:vnp1
+    if (e == cudaSuccess) e = launch_gtvf(s->S, L, s->kmax, 0);  // Eqs. int:gtvf:*
+    if (e == cudaSuccess) e = launch_update(s->S, L, 0);   // Eqs. int:vhatnp2, int:rnp2
   }
-  if (e == cudaSuccess) e = launch_pgrad(s->S, L);    // Eq. int:vnp1
-  if (e == cudaSuccess) e = launch_gtvf(s->S, L, s->kmax, 0);  // Eqs. int:gtvf:*
-  if (e == cudaSuccess) e = launch_update(s->S, L, 0);   // Eqs. int:vhatnp2, int:rnp2
+  // next time step (Sec. 3.2) and the simulated time
+  if (e == cudaSuccess && s->adaptive) e = launch_speed_max(s->S, L, 1);
+  if (e == cudaSuccess) e = launch_adapt_dt(s->S, L);
   return e;
 }
 
@@ -426,6 +431,8 @@ int setup_case(sisph_t s, int c, const sisph_particles &P, const sisph_case_para
   D.pref_mode = q.pref_mode;
   D.K = q.gtvf_K;
   D.p_ref0 = q.p_ref;
+  D.adaptive = q.adaptive_dt;
+  D.dt_visc = q.nu > 0.0 ? 0.25 * q.h * q.h / q.nu : INFINITY;
   D.cut2 = (3.0 * q.h) * (3.0 * q.h);
   D.eh2 = s->opt.eta * q.h * q.h;
   D.inv_h = 1.0 / q.h;
@@ -522,6 +529,7 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
       return fail(nullptr, SISPH_EINVAL, cs + "max_iter >= 1 and 1 <= gtvf_K <= 64");
     if (q.pref_mode < 0 || q.pref_mode > 2) return fail(nullptr, SISPH_EINVAL, cs + "bad pref_mode");
     if (!(q.gtvf_hfac > 0.0)) return fail(nullptr, SISPH_EINVAL, cs + "gtvf_hfac must be > 0");
+    if (q.adaptive_dt != 0 && q.adaptive_dt != 1) return fail(nullptr, SISPH_EINVAL, cs + "adaptive_dt must be 0 or 1");
     for (int64_t i = 0; i < P.n; ++i) {
       int kd = P.kind ? P.kind[i] : 0;
       if (kd != SISPH_KIND_FLUID && kd != SISPH_KIND_WALL) return fail(nullptr, SISPH_EINVAL, cs + "bad kind");
@@ -613,6 +621,7 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
     wrow += nwc;
     off += P.n;
     s->kmax = std::max(s->kmax, params[c].gtvf_K);
+    s->adaptive = s->adaptive || params[c].adaptive_dt != 0;
   }
   if (key_base >= (1LL << 31) || key_base > (1LL << 26)) {
     delete s;
@@ -677,7 +686,12 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
     e = dalloc(s, &q, cnt * rb);
     *p = q;
   };
-  AR(&S.coef, N * size_t(S.cap));
+  // one 8-byte slot per ELL entry: packed index + FP32 coefficient, or FP64
+  if (e == cudaSuccess) {
+    char *q = nullptr;
+    e = dalloc(s, &q, N * size_t(S.cap) * 8);
+    S.coef = q;
+  }
   AR(&S.prhs, N);
   AR(&S.pwd, N);
   for (int q = 0; q < 4; ++q) AR(&S.pb[q], N);
@@ -704,6 +718,12 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   A(&S.iters_tot, ncases); A(&S.solves, ncases);
   A(&S.pref, ncases); A(&S.pref_set, ncases);
   A(&S.bar, 1);
+  A(&S.tsim, ncases);
+  if (s->adaptive) {
+    for (int k = 0; k < 3; ++k) A(&S.fs1[k], N);
+    A(&S.umax2, ncases);
+    A(&S.fmax2, ncases);
+  }
   A(&S.err, 1);
   A(&s->d_tmp, N);
   A(&s->d_tmp2, N);
@@ -823,6 +843,12 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   if (e == cudaSuccess) e = cudaMemset(S.solves, 0, ncases * sizeof(long long));
   if (e == cudaSuccess) e = cudaMemset(S.nreb, 0, (ncases + 1) * sizeof(long long));
   if (e == cudaSuccess) e = cudaMemset(S.nbody, 0, sizeof(long long));
+  if (e == cudaSuccess) e = cudaMemset(S.tsim, 0, ncases * sizeof(double));
+  if (e == cudaSuccess && s->adaptive) {
+    e = cudaMemset(S.umax2, 0, ncases * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(S.fmax2, 0, ncases * sizeof(unsigned long long));
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMemset(S.fs1[k], 0, N * sizeof(double));
+  }
   if (e == cudaSuccess) e = cudaMemset(S.iters, 0, ncases * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(S.resid, 0, ncases * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(S.lam, 0, ncases * sizeof(double));
@@ -919,17 +945,25 @@ int sisph_compute_density(sisph_t s) {
 int sisph_ppe_solve(sisph_t s, double tol, int32_t max_iter, int32_t *iters, double *residual) {
   if (!valid_handle(s)) return fail(s, SISPH_EINVAL, "invalid handle");
   if (max_iter < 1 || !(tol >= 0.0)) return fail(s, SISPH_EINVAL, "max_iter >= 1 and tol >= 0 required");
-  std::vector<CaseDev> hc = s->hc;
+  // the solve's tolerance and cap on top of the device copy of the cases
+  // (which holds the current, possibly adapted, time steps)
+  std::vector<CaseDev> cur(s->hc.size()), hc;
+  cudaError_t e = cudaMemcpyAsync(cur.data(), s->S.cases, cur.size() * sizeof(CaseDev),
+                                  cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  hc = cur;
   for (auto &c : hc) {
     c.tol = tol;
     c.max_iter = max_iter;
   }
-  cudaError_t e = cudaMemcpyAsync((void *)s->S.cases, hc.data(), hc.size() * sizeof(CaseDev),
-                                  cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync((void *)s->S.cases, hc.data(), hc.size() * sizeof(CaseDev),
+                        cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) e = do_ppe(s);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync((void *)s->S.cases, s->hc.data(), hc.size() * sizeof(CaseDev),
+    e = cudaMemcpyAsync((void *)s->S.cases, cur.data(), cur.size() * sizeof(CaseDev),
                         cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "ppe_solve");
   int rc = check_status(s, true);
   std::vector<int> it(s->ncases);
@@ -1113,6 +1147,10 @@ int sisph_stats(sisph_t s, sisph_case_stats *st) {
   if (e == cudaSuccess) e = cudaMemcpy(tot.data(), S.iters_tot, nc * sizeof(long long), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(sv.data(), S.solves, nc * sizeof(long long), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(rb.data(), S.nreb, nc * sizeof(long long), cudaMemcpyDeviceToHost);
+  std::vector<CaseDev> cd(nc);
+  std::vector<double> ts(nc);
+  if (e == cudaSuccess) e = cudaMemcpy(cd.data(), S.cases, nc * sizeof(CaseDev), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(ts.data(), S.tsim, nc * sizeof(double), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(s, e, "stats");
   for (int c = 0; c < nc; ++c) {
     st[c].iters = it[c];
@@ -1123,6 +1161,8 @@ int sisph_stats(sisph_t s, sisph_case_stats *st) {
     st[c].total_iters = tot[c];
     st[c].solves = sv[c];
     st[c].rebuilds = rb[c];
+    st[c].dt = cd[c].dt;
+    st[c].time = ts[c];
   }
   return SISPH_OK;
 }
@@ -1218,7 +1258,7 @@ int sisph_save(sisph_t s, const char *path) {
   if (!valid_handle(s) || !path) return fail(s, SISPH_EINVAL, "invalid handle or path");
   FILE *f = fopen(path, "wb");
   if (!f) return fail(s, SISPH_EINVAL, std::string("cannot open ") + path);
-  const char magic[8] = {'S', 'I', 'S', 'P', 'H', 'C', 'K', '2'};
+  const char magic[8] = {'S', 'I', 'S', 'P', 'H', 'C', 'K', '3'};
   int64_t hdr[3] = {s->n, s->ncases, s->dim};
   bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1;
   std::vector<double> buf(size_t(s->n));
@@ -1240,9 +1280,17 @@ int sisph_save(sisph_t s, const char *path) {
   cudaMemcpy(ps.data(), s->S.pref_set, s->ncases * sizeof(int), cudaMemcpyDeviceToHost);
   cudaMemcpy(&force, s->S.force, sizeof(int), cudaMemcpyDeviceToHost);
   int32_t pending = force != 0;
+  // per case: the next time step (adaptive) and the simulated time
+  std::vector<CaseDev> cd(s->ncases);
+  std::vector<double> dts(s->ncases), ts(s->ncases);
+  cudaMemcpy(cd.data(), s->S.cases, s->ncases * sizeof(CaseDev), cudaMemcpyDeviceToHost);
+  cudaMemcpy(ts.data(), s->S.tsim, s->ncases * sizeof(double), cudaMemcpyDeviceToHost);
+  for (int c = 0; c < s->ncases; ++c) dts[c] = cd[c].dt;
   ok = ok && fwrite(pr.data(), sizeof(double), pr.size(), f) == pr.size();
   ok = ok && fwrite(ps.data(), sizeof(int), ps.size(), f) == ps.size();
   ok = ok && fwrite(&pending, sizeof(pending), 1, f) == 1;
+  ok = ok && fwrite(dts.data(), sizeof(double), dts.size(), f) == dts.size();
+  ok = ok && fwrite(ts.data(), sizeof(double), ts.size(), f) == ts.size();
   fclose(f);
   return ok ? SISPH_OK : fail(s, SISPH_EINVAL, "write failed");
 }
@@ -1254,7 +1302,7 @@ int sisph_load(sisph_t s, const char *path) {
   char magic[8];
   int64_t hdr[3];
   bool ok = fread(magic, 1, 8, f) == 8 && fread(hdr, sizeof(hdr), 1, f) == 1;
-  if (!ok || memcmp(magic, "SISPHCK2", 8) != 0 || hdr[0] != s->n || hdr[1] != s->ncases || hdr[2] != s->dim) {
+  if (!ok || memcmp(magic, "SISPHCK3", 8) != 0 || hdr[0] != s->n || hdr[1] != s->ncases || hdr[2] != s->dim) {
     fclose(f);
     return fail(s, SISPH_EINVAL, "checkpoint does not match this handle");
   }
@@ -1273,12 +1321,22 @@ int sisph_load(sisph_t s, const char *path) {
   std::vector<double> pr(s->ncases);
   std::vector<int> ps(s->ncases);
   int32_t pending = 0;
+  std::vector<double> dts(s->ncases), ts(s->ncases);
   ok = fread(pr.data(), sizeof(double), pr.size(), f) == pr.size() &&
-       fread(ps.data(), sizeof(int), ps.size(), f) == ps.size() && fread(&pending, sizeof(pending), 1, f) == 1;
+       fread(ps.data(), sizeof(int), ps.size(), f) == ps.size() && fread(&pending, sizeof(pending), 1, f) == 1 &&
+       fread(dts.data(), sizeof(double), dts.size(), f) == dts.size() &&
+       fread(ts.data(), sizeof(double), ts.size(), f) == ts.size();
   fclose(f);
   if (!ok) return fail(s, SISPH_EINVAL, "short checkpoint");
   cudaError_t e = cudaMemcpy(s->S.pref, pr.data(), s->ncases * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->S.pref_set, ps.data(), s->ncases * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->S.tsim, ts.data(), s->ncases * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    std::vector<CaseDev> cd(s->ncases);
+    e = cudaMemcpy(cd.data(), s->S.cases, s->ncases * sizeof(CaseDev), cudaMemcpyDeviceToHost);
+    for (int c = 0; c < s->ncases; ++c) cd[c].dt = dts[c];
+    if (e == cudaSuccess) e = cudaMemcpy((void *)s->S.cases, cd.data(), s->ncases * sizeof(CaseDev), cudaMemcpyHostToDevice);
+  }
   // sort and skin lists as they were at the saved rebuild positions (or at
   // the current ones if a rebuild was pending), then the refresh the saved
   // run would have made next

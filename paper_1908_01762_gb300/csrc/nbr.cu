@@ -590,6 +590,7 @@ __global__ void k_set_conditional(cudaGraphConditionalHandle h, const int *anyne
 // launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_set_conditional(const State &S, const Launch &L, cudaGraphConditionalHandle h) {
+  if (L.before) L.before(L.ctx, "setcond");
   k_set_conditional<<<1, 1, 0, L.stream>>>(h, S.anyneed);
   if (L.after) L.after(L.ctx, "setcond", 0.0, 1);
   return cudaGetLastError();

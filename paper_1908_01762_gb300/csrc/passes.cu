@@ -3,6 +3,8 @@
 // neighbours from the ELL lists built by nbr.cu.  Template parameter MX
 // selects the MIXED form: FP32 sums over FP32 cell-relative positions, with
 // the FP64 master state updated in FP64.
+#include <math_constants.h>
+
 #include "sisph_internal.h"
 
 namespace sisph {
@@ -273,6 +275,7 @@ __global__ void k_stage1(State S) {
   const double dt = P.dt;
   _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
     double fk = double(f[k]) + P.g[k];
+    if (P.adaptive) S.fs1[k][i] = fk;
     S.us[k][i] = S.u[k][i] + dt * fk;
     double xk = __dadd_rn(S.x[k][i], __dmul_rn(dt, S.ut[k][i]));
     if (P.per[k]) {
@@ -337,7 +340,10 @@ __global__ void k_pgrad(State S) {
       _Pragma("unroll") for (int k = 0; k < DIM; ++k) f[k] += c * d[k];
     }
   })
-  _Pragma("unroll") for (int k = 0; k < DIM; ++k) S.u[k][i] = S.u[k][i] + P.dt * double(f[k]);
+  _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
+    S.u[k][i] = S.u[k][i] + P.dt * double(f[k]);
+    if (P.adaptive) S.fs1[k][i] += double(f[k]);     // total acceleration
+  }
 }
 
 // p_ref = 2 max_i p_i after the first PPE solve (internal flows, Sec. 2.1);
@@ -483,6 +489,7 @@ __global__ void k_pgrad_gtvf1(State S) {
   _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
     unew[k] = S.u[k][i] + dt * double(f[k]);
     S.u[k][i] = unew[k];
+    if (P.adaptive) S.fs1[k][i] += double(f[k]);     // total acceleration
   }
   if (!fused) return;
   const double pref = S.pref[t.c];
@@ -566,6 +573,73 @@ __global__ void k_gather_field(State S, const double *src, double *dst) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= S.n) return;
   dst[i] = src[S.uid[i]];
+}
+
+// ---------------------------------------------------------------------------
+// Adaptive time step (Sec. 3.2).  k_speed_max: per case the maximum over its
+// fluid of |u|^2 (which 0, at the start of the step) or of |f|^2 (which 1,
+// the step's total acceleration), the squares evaluated as u0 u0 + u1 u1 +
+// u2 u2 without contraction; a block reduces its tile and raises the case's
+// maximum with one 64-bit atomic (non-negative doubles order as integers).
+// k_adapt_dt: dt^{n+1} = min(0.25 h/max|u|, 0.25 sqrt(h/max|f|), 0.25 h^2/nu),
+// a limit with a zero denominator left out (dt kept if all are); the
+// maxima are cleared for the next step and the simulated time advances.
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void k_speed_max(State S, int which) {
+  const Tile &t = S.ftiles[blockIdx.x];
+  const CaseDev &P = S.cases[t.c];
+  if (!P.adaptive) return;
+  const int i = t.beg + threadIdx.x;
+  double v = 0.0;
+  if (i < t.end) {
+    double a[3] = {0.0, 0.0, 0.0};
+    _Pragma("unroll") for (int k = 0; k < DIM; ++k) a[k] = which ? S.fs1[k][i] : S.u[k][i];
+    v = __dadd_rn(__dadd_rn(__dmul_rn(a[0], a[0]), __dmul_rn(a[1], a[1])), __dmul_rn(a[2], a[2]));
+  }
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __shared__ double sh[32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = sh[0];
+    for (int w = 1; w < int(blockDim.x >> 5); ++w) m = fmax(m, sh[w]);
+    unsigned long long *dst = (which ? S.fmax2 : S.umax2) + t.c;
+    atomicMax(dst, static_cast<unsigned long long>(__double_as_longlong(m)));
+  }
+}
+
+__global__ void k_adapt_dt(State S) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= S.ncases) return;
+  CaseDev &P = const_cast<CaseDev &>(S.cases[c]);
+  S.tsim[c] += P.dt;
+  if (!P.adaptive) return;
+  const double umax = sqrt(__longlong_as_double(static_cast<long long>(S.umax2[c])));
+  const double fmax = sqrt(__longlong_as_double(static_cast<long long>(S.fmax2[c])));
+  double dt = CUDART_INF;
+  if (umax > 0.0) dt = fmin(dt, 0.25 * P.h / umax);
+  if (fmax > 0.0) dt = fmin(dt, 0.25 * sqrt(P.h / fmax));
+  dt = fmin(dt, P.dt_visc);
+  if (isfinite(dt)) P.dt = dt;
+  S.umax2[c] = 0ull;
+  S.fmax2[c] = 0ull;
+}
+
+cudaError_t launch_speed_max(const State &S, const Launch &L, int which) {
+  if (S.nft == 0) return cudaSuccess;
+  if (L.before) L.before(L.ctx, "speed_max");
+  if (S.dim == 2) k_speed_max<2><<<S.nft, S.T, 0, L.stream>>>(S, which);
+  else k_speed_max<3><<<S.nft, S.T, 0, L.stream>>>(S, which);
+  if (L.after) L.after(L.ctx, "speed_max", double(S.nf), 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adapt_dt(const State &S, const Launch &L) {
+  if (L.before) L.before(L.ctx, "adapt_dt");
+  k_adapt_dt<<<(S.ncases + 127) / 128, 128, 0, L.stream>>>(S);
+  if (L.after) L.after(L.ctx, "adapt_dt", double(S.ncases), 1);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -22,6 +22,34 @@ __device__ __forceinline__ void kahan_add(R &sum, R &comp, R v) {
 }
 
 // ---------------------------------------------------------------------------
+// Stored PPE coefficients, one per ELL slot.  MIXED: the neighbour index and
+// the FP32 coefficient packed in 8 bytes, so that a sweep streams one array
+// with one load per slot; FP64: the coefficient alone (the index comes from
+// the neighbour list).
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void store_coef(void *base, long long o, int j, R fac) {
+  if constexpr (std::is_same<R, float>::value)
+    static_cast<uint2 *>(base)[o] = make_uint2(unsigned(j), __float_as_uint(fac));
+  else
+    static_cast<double *>(base)[o] = fac;
+}
+
+// Slot o of row i: neighbour j and coefficient (a slot past the row's end,
+// in[u] false, reads the row itself with a zero coefficient).
+template <typename R>
+__device__ __forceinline__ void load_coef(const State &S, long long o, bool in, int i, int &j, R &cf) {
+  if constexpr (std::is_same<R, float>::value) {
+    const uint2 v = in ? static_cast<const uint2 *>(S.coef)[o] : make_uint2(unsigned(i), 0u);
+    j = int(v.x);
+    cf = __uint_as_float(v.y);
+  } else {
+    j = in ? int(S.nbr[o] & kIdxMask) : i;
+    cf = in ? static_cast<const double *>(S.coef)[o] : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Tile dependencies of the point-to-point sweeps: the set of other tiles
 // whose rows a tile's PPE rows read, collected in a shared-memory hash set
 // while the rows are set up, then written as a list (ndeps = -1 when the
@@ -104,7 +132,6 @@ __global__ void k_setup_fluid(State S) {
     const R idt = R(1.0 / P.dt);
     const R four_iri = R(4) / ri;
     R rhs = R(0), rc = R(0), dg = R(0), dc = R(0);
-    R *coef = static_cast<R *>(S.coef);
     ROW_CHUNKS(S, i, {
       const int k = _q0 + _u;
       int j = int(e & kIdxMask);
@@ -141,7 +168,7 @@ __global__ void k_setup_fluid(State S) {
         }
       }
       if (valid) {
-        coef[(long long)k * _n + i] = fac;
+        store_coef<R>(S.coef, (long long)k * _n + i, j, fac);
         if (j != i) {
           const int dt = S.tile_of[j];
           if (dt != int(blockIdx.x)) deps.insert(dt);
@@ -351,19 +378,14 @@ __device__ __forceinline__ R wall_pressure(const State &S, const R *pc, int r, i
 // coefficient.
 template <typename R>
 __device__ __forceinline__ R jacobi_sum(const State &S, const R *pc, int i, R acc, int cnt) {
-  const R *coef = static_cast<const R *>(S.coef);
   const long long n = S.n;
   for (int q0 = 0; q0 < cnt; q0 += 8) {
-    unsigned e[8];
+    int jj[8];
     R cf[8];
-    _Pragma("unroll") for (int u = 0; u < 8; ++u) {
-      const int q = q0 + u;
-      const long long o = (long long)q * n + i;
-      e[u] = q < cnt ? S.nbr[o] : unsigned(i);
-      cf[u] = q < cnt ? coef[o] : R(0);
-    }
+    _Pragma("unroll") for (int u = 0; u < 8; ++u)
+      load_coef<R>(S, (long long)(q0 + u) * n + i, q0 + u < cnt, i, jj[u], cf[u]);
     R pj[8];
-    _Pragma("unroll") for (int u = 0; u < 8; ++u) pj[u] = pc[e[u] & kIdxMask];
+    _Pragma("unroll") for (int u = 0; u < 8; ++u) pj[u] = pc[jj[u]];
     _Pragma("unroll") for (int u = 0; u < 8; ++u) acc += cf[u] * pj[u];
   }
   return acc;
@@ -534,7 +556,6 @@ __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
   const int T = blockDim.x;
   const int nc = S.ncases;
   const R om1 = R(1.0 - S.omega);
-  const R *coef = static_cast<const R *>(S.coef);
   const R *prhs = static_cast<const R *>(S.prhs);
   const R *pwd = static_cast<const R *>(S.pwd);
   const R *wc = static_cast<const R *>(S.wcoef);
@@ -627,16 +648,12 @@ __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
         R acc = prhs[i];
         const int cnt = S.ncnt[i];
         for (int q0 = 0; q0 < cnt; q0 += 8) {
-          unsigned e[8];
+          int jj[8];
           R cf[8];
-          _Pragma("unroll") for (int u = 0; u < 8; ++u) {
-            const int q = q0 + u;
-            const long long o = (long long)q * n + i;
-            e[u] = q < cnt ? S.nbr[o] : unsigned(i);
-            cf[u] = q < cnt ? coef[o] : R(0);
-          }
+          _Pragma("unroll") for (int u = 0; u < 8; ++u)
+            load_coef<R>(S, (long long)(q0 + u) * n + i, q0 + u < cnt, i, jj[u], cf[u]);
           R pj[8];
-          _Pragma("unroll") for (int u = 0; u < 8; ++u) pj[u] = pc[e[u] & kIdxMask];
+          _Pragma("unroll") for (int u = 0; u < 8; ++u) pj[u] = pc[jj[u]];
           _Pragma("unroll") for (int u = 0; u < 8; ++u) acc += cf[u] * pj[u];
         }
         R po = pc[i];

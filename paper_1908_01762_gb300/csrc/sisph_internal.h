@@ -44,6 +44,8 @@ struct CaseDev {
   double h, dt, rho0, nu, g[3], alpha, c0, tol, hfac;
   int max_iter, pgrad_symm, free_surface, ustar_slip, pref_mode, K;
   double p_ref0;
+  int adaptive;            // next dt from max|u^n|, max|f^n| (Sec. 3.2)
+  double dt_visc;          // 0.25 h^2 / nu (infinite without viscosity)
   // derived constants
   double cut2;             // (3h)^2, evaluated as (3*h)*(3*h)
   double skin;             // Verlet skin s: lists hold every j within 3h + s
@@ -113,7 +115,7 @@ struct State {
   long long *nreb;         // rebuilds per case; [ncases]: refreshes that rebuilt
   long long *nbody;        // rebuild groups run inside conditional graph nodes
   // PPE
-  void *coef;              // fac_ij per ELL slot (double or float)
+  void *coef;              // fac_ij per ELL slot: FP64, or {j, FP32 fac} (MIXED)
   void *prhs;              // RHS_i (active) else 0
   void *pwd;               // omega / D_ii (active) else 0
   void *pb[4];             // pressure buffers: p^k in pb[k % 2] (grid barrier
@@ -144,6 +146,10 @@ struct State {
   double *dg[2][3];        // FP64 displacement ping-pong
   float4 *dgf[2];          // FP32 displacement ping-pong
   double *vgt[3];          // sub-step velocity
+  // adaptive time step (only allocated when a case uses it)
+  double *fs1[3];          // per fluid particle: total acceleration of the step
+  unsigned long long *umax2, *fmax2;  // per case: max |u^n|^2, max |f^n|^2 (bits)
+  double *tsim;            // per case: simulated time
   // debug
   long long barrier_budget;
   int debug_skip_barrier;
@@ -320,6 +326,8 @@ cudaError_t launch_pref(const State &S, const Launch &L);
 cudaError_t launch_gtvf(const State &S, const Launch &L, int kmax, int skip_k1);
 cudaError_t launch_update(const State &S, const Launch &L, int skip_k1);
 cudaError_t launch_pgrad_gtvf1(const State &S, const Launch &L);
+cudaError_t launch_speed_max(const State &S, const Launch &L, int which);
+cudaError_t launch_adapt_dt(const State &S, const Launch &L);
 cudaError_t launch_scatter_field(const State &S, const Launch &L, const void *src, int is_float,
                                  int stride_f4, int comp, double *dst_user);
 cudaError_t launch_gather_field(const State &S, const Launch &L, const double *src_user, double *dst);

@@ -45,7 +45,8 @@ class sisph_case_params(C.Structure):
                 ("g", C.c_double * 3), ("alpha", C.c_double), ("c0", C.c_double),
                 ("tol", C.c_double), ("max_iter", C.c_int32), ("pgrad_symm", C.c_int32),
                 ("free_surface", C.c_int32), ("ustar_slip", C.c_int32), ("pref_mode", C.c_int32),
-                ("p_ref", C.c_double), ("gtvf_hfac", C.c_double), ("gtvf_K", C.c_int32)]
+                ("p_ref", C.c_double), ("gtvf_hfac", C.c_double), ("gtvf_K", C.c_int32),
+                ("adaptive_dt", C.c_int32)]
 
 
 class sisph_options(C.Structure):
@@ -61,7 +62,8 @@ class sisph_options(C.Structure):
 class sisph_case_stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("residual", C.c_double),
                 ("lambda_", C.c_double), ("p_ref", C.c_double), ("total_iters", C.c_int64),
-                ("solves", C.c_int64), ("rebuilds", C.c_int64)]
+                ("solves", C.c_int64), ("rebuilds", C.c_int64), ("dt", C.c_double),
+                ("time", C.c_double)]
 
 
 _lib = None
@@ -171,6 +173,7 @@ def case_params_from_dict(prm):
         setattr(q, key, float(prm[key]))
     for key in ("max_iter", "pgrad_symm", "free_surface", "ustar_slip", "pref_mode", "gtvf_K"):
         setattr(q, key, int(prm[key]))
+    q.adaptive_dt = int(prm.get("adaptive_dt", 0))
     for k in range(3):
         q.g[k] = float(prm["g"][k])
     return q

@@ -188,3 +188,51 @@ def test_flat_wall_normals(oracle_lib):
     assert np.all(nx[~wall] == 0) and np.all(ny[~wall] == 0)
     mag = np.hypot(nx, ny)
     assert np.all((np.abs(mag - 1) < 1e-12) | (mag == 0))
+
+
+def test_adaptive_time_step_in_free_fall(oracle_lib):
+    """Adaptive dt (Sec. 3.2) against the closed form of a free fall: the only
+    force is g, so max|f| = g and max|u^n| = g t_n.  The step after one
+    starting at rest is force-limited, 0.25 sqrt(h/g); once g t_n exceeds
+    sqrt(g h) the CFL limit 0.25 h/(g t_n) takes over.  The position update
+    r^{n+1} = r^n + dt (u~^{n+1} + u~^n)/2 is exact for constant acceleration
+    with any sequence of steps: y = y0 - g t^2 / 2."""
+    import math
+    case = workloads.free_fall_blob()
+    h, g = case["params"]["h"], 9.81
+    sim = oracle.Sim(case)
+    dts, starts, t = [], [], 0.0
+    for _ in range(12):
+        starts.append(t)
+        rc, d = sim.step(1)
+        dts.append(d[0].dt)
+        t += d[0].dt
+    assert np.all(sim.get("p") == 0.0)
+    dt_f = 0.25 * math.sqrt(h / g)
+    assert dts[0] == case["params"]["dt"]
+    kinds = []
+    for k in range(1, len(dts)):
+        t_prev = starts[k - 1]                      # u at the start of step k-1 is g t_prev
+        cfl = 0.25 * h / (g * t_prev) if t_prev > 0 else math.inf
+        expect = min(dt_f, cfl)
+        kinds.append("cfl" if cfl < dt_f else "force")
+        assert abs(dts[k] - expect) <= 1e-12 * expect, (k, dts[k], expect)
+    assert "cfl" in kinds and "force" in kinds      # both limits were exercised
+    assert np.allclose(sim.get("v"), -g * t, rtol=1e-12, atol=0)
+    assert np.allclose(sim.get("y"), case["y"] - 0.5 * g * t * t, rtol=0, atol=1e-12)
+    assert np.allclose(sim.get("x"), case["x"], rtol=0, atol=1e-15)
+
+
+def test_adaptive_time_step_tgv_first_step_is_cfl(oracle_lib):
+    """TGV: the step after step 0 follows the CFL limit of the initial speed
+    field, 0.25 h / max|u^0| (max over the lattice from the initial
+    condition), which is below the force and viscous limits here."""
+    case = workloads.taylor_green(50)
+    case["params"] = dict(case["params"], adaptive_dt=1)
+    sim = oracle.Sim(case)
+    rc, d = sim.step(2)
+    umax0 = float(np.max(np.hypot(case["u"], case["v"])))
+    h = case["params"]["h"]
+    assert d[0].dt == case["params"]["dt"]
+    assert abs(d[1].dt - 0.25 * h / umax0) <= 1e-13 * d[1].dt
+    assert d[1].dt < 0.25 * h * h / case["params"]["nu"]

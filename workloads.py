@@ -46,6 +46,7 @@ def _params(**kw):
         pref_mode=PREF_FIXED, p_ref=0.0,
         gtvf_hfac=1.0, gtvf_K=1,        # h~ = hfac * h, K GTVF sub-steps
         ustar_slip=1,                   # slip ghost velocity for u* in the PPE
+        adaptive_dt=0,                  # 1: next dt from max|u|, max|f| (Sec. 3.2)
     )
     base.update(kw)
     base["g"] = tuple(float(v) for v in base["g"])
@@ -290,6 +291,23 @@ def still_tank_2d(nx=20, ny=20, dx=0.05, layers=3, rho0=1000.0, g=9.81, tol=1e-3
     return _case(2, x, y, None, np.zeros(n), np.zeros(n), None, np.full(n, rho0 * dx * dx),
                  np.full(n, rho0), p, kind, None, (-pad, -pad, 0),
                  (nx * dx + pad, H * 2, 1), (0, 0, 0), prm, f"tank{nx}x{ny}")
+
+
+def free_fall_blob(n_side=4, dx=0.05, spacing=2.2, g=9.81, rho0=1000.0, adaptive=True):
+    """A sparse square of fluid particles (spacing * dx apart, so every
+    particle is below the free-surface density and keeps p = 0) falling
+    freely in a large closed box without walls: no viscosity, no artificial
+    viscosity, zero background pressure.  The only force is gravity, so the
+    motion and the adaptive time steps (Sec. 3.2) have closed forms."""
+    x, y = _lattice2(n_side, n_side, spacing * dx, x0=4.0, y0=4.0)
+    n = x.size
+    h = dx
+    prm = _params(h=h, dt=0.25 * math.sqrt(h / g), rho0=rho0, nu=0.0, g=(0.0, -g, 0.0),
+                  alpha=0.0, tol=1e-3, free_surface=1, pref_mode=PREF_FIXED, p_ref=0.0,
+                  adaptive_dt=1 if adaptive else 0)
+    return _case(2, x, y, None, np.zeros(n), np.zeros(n), None, np.full(n, rho0 * dx * dx),
+                 np.full(n, rho0), np.zeros(n), np.zeros(n, np.int32), None, (0, 0, 0),
+                 (10, 10, 1), (0, 0, 0), prm, f"free_fall{n_side}")
 
 
 def batch_ensemble(ncases=64, seed=1762, nmin=50, nmax=300, total=(2.3e6, 2.7e6),
