@@ -43,7 +43,7 @@ class Params(C.Structure):
         ("pgrad_symm", C.c_int32), ("free_surface", C.c_int32), ("ustar_slip", C.c_int32),
         ("pref_mode", C.c_int32), ("p_ref", C.c_double), ("gtvf_hfac", C.c_double),
         ("gtvf_K", C.c_int32), ("residual_form", C.c_int32), ("brute_neighbors", C.c_int32),
-        ("adaptive_dt", C.c_int32),
+        ("adaptive_dt", C.c_int32), ("ppe_solver", C.c_int32),
     ]
 
 
@@ -138,7 +138,7 @@ def make_params(case, **over) -> Params:
     for key in ("eta", "omega", "fs_ratio"):
         if key in prm:
             setattr(P, key, float(prm[key]))
-    for key in ("min_iter", "residual_form", "brute_neighbors", "adaptive_dt"):
+    for key in ("min_iter", "residual_form", "brute_neighbors", "adaptive_dt", "ppe_solver"):
         if key in prm:
             setattr(P, key, int(prm[key]))
     return P

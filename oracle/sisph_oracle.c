@@ -739,6 +739,143 @@ void or_ppe_apply(const or_sim *s, const double *p, double *out) {
   }
 }
 
+/* ---------------------------------------------------------------------------
+ * BiCGStab (van der Vorst 1992) for the PPE, the Krylov alternative the
+ * paper mentions beside its Jacobi iterations (Sec. 3.1).  Reading: it
+ * solves the linear system the Jacobi iteration converges to,
+ *   D_ii p_i - sum_j fac_ij p_j = RHS_i   (active fluid i),  p_i = 0 (inactive),
+ * with each wall pressure replaced by its extrapolation (Eq. p-shepard)
+ *   p_w = (sum_f W_wf p_f + H_w) / S_w,
+ * whose affine part H_w / S_w moves to the right-hand side; the free-surface
+ * clamp p_w >= 0 is not linear and is applied only in the final wall update,
+ * as after the Jacobi sweeps.  Stopping rule: the Jacobi test of Eq.
+ * convergence on the update of each iteration,
+ *   sum_i |x^{k+1}_i - x^k_i| / max(Lambda, sum_i |x^{k+1}_i|) < tol
+ * (at least min_iter, at most max_iter iterations), so that both solvers stop
+ * at the same epsilon.  Dot products run over the fluid particles.
+ * Without a free-surface (Dirichlet) row -- periodic or enclosed flows -- the
+ * system is singular (constant pressures are in its null space) and, with a
+ * right-hand side that is consistent only up to rounding and the slight
+ * asymmetry of fac_ij, a Krylov solve diverges; such a case is solved by the
+ * Jacobi iteration instead (reading).
+ * ------------------------------------------------------------------------- */
+static void or_wall_linear(const or_sim *s, double *x, int with_h) {
+  for (int64_t i = 0; i < s->n; ++i) {
+    if (s->kind[i] != WALL) continue;
+    double acc = 0.0;
+    for (int64_t t = s->nstart[i]; t < s->nstart[i + 1]; ++t) {
+      int64_t j = s->nidx[t];
+      if (s->kind[j] != FLUID) continue;
+      acc += x[j] * s->fac[t];
+    }
+    if (with_h) acc += s->wh[i];
+    x[i] = (s->ws[i] > 0.0) ? acc / s->ws[i] : 0.0;
+  }
+}
+
+/* y = A x over fluid rows (walls of x overwritten by their linear part). */
+static void or_apply_linear(const or_sim *s, double *x, double *y) {
+  or_wall_linear(s, x, 0);
+  for (int64_t i = 0; i < s->n; ++i) {
+    y[i] = 0.0;
+    if (s->kind[i] != FLUID) continue;
+    if (!s->active[i]) { y[i] = x[i]; continue; }
+    double acc = s->diag[i] * x[i];
+    for (int64_t t = s->nstart[i]; t < s->nstart[i + 1]; ++t) acc -= s->fac[t] * x[s->nidx[t]];
+    y[i] = acc;
+  }
+}
+
+static double or_fdot(const or_sim *s, const double *a, const double *b) {
+  double acc = 0.0;
+  for (int64_t i = 0; i < s->n; ++i)
+    if (s->kind[i] == FLUID) acc += a[i] * b[i];
+  return acc;
+}
+
+void or_ppe_bicgstab(or_sim *s, or_diag *d) {
+  const or_params *P = &s->prm;
+  const int64_t n = s->n;
+  int64_t dirichlet = 0;
+  for (int64_t i = 0; i < n; ++i) dirichlet += (s->kind[i] == FLUID && !s->active[i]);
+  if (dirichlet == 0) {
+    or_ppe_iterate(s, d);
+    return;
+  }
+  double *x = or_alloc(n), *b = or_alloc(n), *r = or_alloc(n), *rh = or_alloc(n);
+  double *pv = or_alloc(n), *v = or_alloc(n), *sv = or_alloc(n), *tv = or_alloc(n);
+  int64_t nfluid = 0;
+  for (int64_t i = 0; i < n; ++i) nfluid += (s->kind[i] == FLUID);
+  // right-hand side: RHS plus the affine part of the wall extrapolation
+  double *w0 = or_alloc(n);
+  or_wall_linear(s, w0, 1);
+  for (int64_t i = 0; i < n; ++i) {
+    if (s->kind[i] != FLUID || !s->active[i]) continue;
+    double acc = s->rhs[i];
+    for (int64_t t = s->nstart[i]; t < s->nstart[i + 1]; ++t) {
+      int64_t j = s->nidx[t];
+      if (s->kind[j] == WALL) acc += s->fac[t] * w0[j];
+    }
+    b[i] = acc;
+  }
+  for (int64_t i = 0; i < n; ++i) x[i] = (s->kind[i] == FLUID && s->active[i]) ? s->p[i] : 0.0;
+  or_apply_linear(s, x, r);
+  for (int64_t i = 0; i < n; ++i) {
+    r[i] = (s->kind[i] == FLUID) ? b[i] - r[i] : 0.0;
+    rh[i] = r[i];
+  }
+  double rho_prev = 1.0, alpha = 1.0, omega = 1.0;
+  int32_t k = 0;
+  double res = 0.0;
+  int conv = 0, bad = 0;
+  while (1) {
+    // breakdown guards: r = 0 means x solves the system; (r^, r) = 0 or
+    // (r^, v) = 0 otherwise stops the iteration (not converged)
+    const double rho = or_fdot(s, rh, r);
+    if (rho == 0.0) {
+      if (or_fdot(s, r, r) == 0.0) { conv = 1; res = 0.0; }
+      break;
+    }
+    const double beta = (rho / rho_prev) * (alpha / omega);
+    for (int64_t i = 0; i < n; ++i)
+      if (s->kind[i] == FLUID) pv[i] = r[i] + beta * (pv[i] - omega * v[i]);
+    or_apply_linear(s, pv, v);
+    const double rv = or_fdot(s, rh, v);
+    if (rv == 0.0) break;
+    alpha = rho / rv;
+    for (int64_t i = 0; i < n; ++i)
+      if (s->kind[i] == FLUID) sv[i] = r[i] - alpha * v[i];
+    or_apply_linear(s, sv, tv);
+    const double tt = or_fdot(s, tv, tv);
+    omega = tt > 0.0 ? or_fdot(s, tv, sv) / tt : 0.0;
+    double num = 0.0, den = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      if (s->kind[i] != FLUID) continue;
+      const double dx = alpha * pv[i] + omega * sv[i];
+      x[i] += dx;
+      r[i] = sv[i] - omega * tv[i];
+      num += fabs(dx);
+      den += fabs(x[i]);
+    }
+    rho_prev = rho;
+    ++k;
+    const double lam = (P->residual_form == 1) ? (double)nfluid * s->lambda : s->lambda;
+    const double dd = (lam > den) ? lam : den;
+    res = (dd > 0.0) ? num / dd : num;
+    if (!isfinite(res)) { bad = 1; break; }
+    if (k >= P->min_iter && res < P->tol) { conv = 1; break; }
+    if (k >= P->max_iter) break;
+  }
+  for (int64_t i = 0; i < n; ++i)
+    if (s->kind[i] == FLUID) s->p[i] = x[i];
+  or_wall_pressure(s);
+  if (d) {
+    d->iters = k; d->residual = res; d->lambda = s->lambda;
+    d->converged = conv; d->nonfinite = bad;
+  }
+  free(x); free(b); free(r); free(rh); free(pv); free(v); free(sv); free(tv); free(w0);
+}
+
 int64_t or_ppe_export(const or_sim *s, double *diag, double *rhs, int32_t *active,
                       double *fac, double *wall_s, double *wall_h, double *wall_w) {
   int64_t tot = s->nstart[s->n];
@@ -876,14 +1013,13 @@ int32_t or_ppe_solve(or_sim *s, double tol, int32_t max_iter, or_diag *d) {
   s->prm.max_iter = max_iter;
   or_ghost_velocity(s, s->prm.ustar_slip);
   or_ppe_setup(s);
-  or_ppe_iterate(s, d);
+  if (s->prm.ppe_solver == 1) or_ppe_bicgstab(s, d);
+  else or_ppe_iterate(s, d);
   s->prm.tol = t0;
   s->prm.max_iter = m0;
   return d->nonfinite ? -5 : (d->converged ? 0 : -4);
 }
 
-/* One time step of Algorithm 1 (two neighbour builds: at r^n for stage 1 and
- * at r* for stage 2, as in the two stages of Listing 1). */
 /* ---------------------------------------------------------------------------
  * Adaptive time step (Sec. 3.2): from the maximum fluid speed max|u^n| at
  * the start of step n and the maximum total acceleration max|f^n| of that
@@ -902,6 +1038,8 @@ static double or_next_dt(const or_params *P, double umax, double fmax) {
   return isfinite(dt) ? dt : P->dt;
 }
 
+/* One time step of Algorithm 1 (two neighbour builds: at r^n for stage 1 and
+ * at r* for stage 2, as in the two stages of Listing 1). */
 int32_t or_step(or_sim *s, int32_t nsteps, or_diag *d) {
   int32_t rc = 0;
   for (int32_t it = 0; it < nsteps; ++it) {
@@ -922,7 +1060,8 @@ int32_t or_step(or_sim *s, int32_t nsteps, or_diag *d) {
     or_ppe_setup(s);
     or_diag dd;
     memset(&dd, 0, sizeof(dd));
-    or_ppe_iterate(s, &dd);
+    if (s->prm.ppe_solver == 1) or_ppe_bicgstab(s, &dd);
+    else or_ppe_iterate(s, &dd);
     if (!s->pref_set) {
       double mx = 0.0;
       int first = 1;

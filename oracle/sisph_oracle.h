@@ -43,6 +43,7 @@ typedef struct {
   int32_t residual_form;    /* 0: max(Lambda, sum|p|), 1: max(N_F Lambda, sum|p|) */
   int32_t brute_neighbors;  /* 1: O(N^2) search, 0: cell list */
   int32_t adaptive_dt;      /* 1: next dt from max|u^n| and max|f^n| (Sec. 3.2) */
+  int32_t ppe_solver;       /* 0 damped Jacobi (Eq. p-sor), 1 BiCGStab */
 } or_params;
 
 typedef struct {
@@ -89,6 +90,7 @@ void or_ghost_velocity(or_sim *s, int32_t slip);
 void or_stage1(or_sim *s);
 void or_ppe_setup(or_sim *s);
 void or_ppe_iterate(or_sim *s, or_diag *d);
+void or_ppe_bicgstab(or_sim *s, or_diag *d);
 void or_ppe_apply(const or_sim *s, const double *p, double *out);
 int64_t or_ppe_export(const or_sim *s, double *diag, double *rhs, int32_t *active,
                       double *fac, double *wall_s, double *wall_h, double *wall_w);
