@@ -97,6 +97,11 @@ typedef struct {
   int32_t adaptive_dt;          /* 1: the next step's dt from max|u^n| and max|f^n|
                                    (Sec. 3.2): min(0.25 h/max|u|, 0.25 sqrt(h/max|f|),
                                    0.25 h^2/nu); dt is then the first step's */
+  int32_t ppe_solver;           /* 0 damped Jacobi (Eq. p-sor, the paper's method);
+                                   1 BiCGStab (van der Vorst) on the same stored
+                                   coefficients and stopping test, used when the
+                                   case has a free-surface row (else its system is
+                                   singular and the Jacobi sweeps run) */
 } sisph_case_params;
 
 /* Solver-wide options.  Defaults from sisph_default_options(). */

@@ -11,8 +11,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsisph.so")
-SOURCES = ["nbr.cu", "passes.cu", "ppe.cu", "api.cu", "noalloc.cu"]
-HEADERS = [os.path.join(CSRC, "sisph_internal.h"), os.path.join(ROOT, "include", "sisph.h")]
+SOURCES = ["nbr.cu", "passes.cu", "ppe.cu", "krylov.cu", "api.cu", "noalloc.cu"]
+HEADERS = [os.path.join(CSRC, "sisph_internal.h"), os.path.join(CSRC, "ppe_sync.cuh"),
+           os.path.join(ROOT, "include", "sisph.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

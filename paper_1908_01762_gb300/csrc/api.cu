@@ -60,6 +60,8 @@ struct sisph_s {
   int kmax = 1;
   int grid = 1;
   bool adaptive = false;           // some case adapts its time step
+  bool krylov = false;             // some case asks for BiCGStab
+  int grid_k = 1;                  // BiCGStab kernel grid
   // the captured step
   cudaGraphExec_t gexec = nullptr;
   bool graph_failed = false;
@@ -286,7 +288,9 @@ cudaError_t do_ppe(sisph_t s) {
   Launch L = mk_launch(s);
   cudaError_t e = launch_ghost(s->S, L, 1);
   if (e == cudaSuccess) e = launch_ppe_setup(s->S, L);
-  if (e == cudaSuccess) e = launch_ppe_sweeps(s->S, L, s->grid);
+  if (e == cudaSuccess) e = launch_ppe_reset(s->S, L);
+  if (e == cudaSuccess && s->krylov) e = launch_ppe_krylov(s->S, L, s->grid_k);   // BiCGStab cases
+  if (e == cudaSuccess) e = launch_ppe_sweeps(s->S, L, s->grid);                   // the rest
   return e;
 }
 
@@ -328,7 +332,8 @@ int check_status(sisph_t s, bool sweeps_ran) {
     if (e != cudaSuccess) return cuda_fail(s, e, "status read");
   }
   cudaMemsetAsync(s->S.err, 0, sizeof(int), s->stream);
-  if (bar_err) return fail(s, SISPH_ETIMEOUT, "persistent PPE kernel: grid barrier wait exceeded its budget");
+  if (bar_err || (err & kErrTimeout))
+    return fail(s, SISPH_ETIMEOUT, "persistent PPE kernel: grid barrier wait exceeded its budget");
   if (err & kErrCapacity)
     return fail(s, SISPH_ECAPACITY, "a particle has more neighbours than the neighbour capacity");
   if (err & kErrNonFinite) return fail(s, SISPH_ENONFINITE, "non-finite PPE residual");
@@ -432,6 +437,7 @@ int setup_case(sisph_t s, int c, const sisph_particles &P, const sisph_case_para
   D.K = q.gtvf_K;
   D.p_ref0 = q.p_ref;
   D.adaptive = q.adaptive_dt;
+  D.solver = q.ppe_solver;
   D.dt_visc = q.nu > 0.0 ? 0.25 * q.h * q.h / q.nu : INFINITY;
   D.cut2 = (3.0 * q.h) * (3.0 * q.h);
   D.eh2 = s->opt.eta * q.h * q.h;
@@ -530,6 +536,7 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
     if (q.pref_mode < 0 || q.pref_mode > 2) return fail(nullptr, SISPH_EINVAL, cs + "bad pref_mode");
     if (!(q.gtvf_hfac > 0.0)) return fail(nullptr, SISPH_EINVAL, cs + "gtvf_hfac must be > 0");
     if (q.adaptive_dt != 0 && q.adaptive_dt != 1) return fail(nullptr, SISPH_EINVAL, cs + "adaptive_dt must be 0 or 1");
+    if (q.ppe_solver != 0 && q.ppe_solver != 1) return fail(nullptr, SISPH_EINVAL, cs + "ppe_solver must be 0 or 1");
     for (int64_t i = 0; i < P.n; ++i) {
       int kd = P.kind ? P.kind[i] : 0;
       if (kd != SISPH_KIND_FLUID && kd != SISPH_KIND_WALL) return fail(nullptr, SISPH_EINVAL, cs + "bad kind");
@@ -622,6 +629,11 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
     off += P.n;
     s->kmax = std::max(s->kmax, params[c].gtvf_K);
     s->adaptive = s->adaptive || params[c].adaptive_dt != 0;
+    s->krylov = s->krylov || params[c].ppe_solver == 1;
+  }
+  if (s->krylov && ncases > 1024) {
+    delete s;
+    return fail(nullptr, SISPH_EINVAL, "BiCGStab cases: at most 1024 cases per handle");
   }
   if (key_base >= (1LL << 31) || key_base > (1LL << 26)) {
     delete s;
@@ -719,6 +731,12 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   A(&S.pref, ncases); A(&S.pref_set, ncases);
   A(&S.bar, 1);
   A(&S.tsim, ncases);
+  A(&S.inact, ncases);
+  if (s->krylov) {
+    for (int q = 0; q < 6; ++q) AR(&S.kv[q], N);
+    A(&S.kpart, 4 * size_t(std::max(1, S.nft)));
+    A(&S.kscal, 8 * size_t(ncases));
+  }
   if (s->adaptive) {
     for (int k = 0; k < 3; ++k) A(&S.fs1[k], N);
     A(&S.umax2, ncases);
@@ -875,6 +893,10 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   int bps2 = ppe_max_blocks_per_sm(S, S.T, true);
   if (bps2 < 1) bps2 = 1;
   S.grid_cap_p2p = bps2 * nsm;
+  if (s->krylov) {
+    int bk = krylov_max_blocks_per_sm(S, S.T);
+    s->grid_k = std::max(1, std::min(s->grid, std::max(1, bk) * nsm));
+  }
   int want = std::max({S.nft, int((s->nw + S.T - 1) / S.T), ncases, 1});
   s->grid = std::min(want, bps * nsm);
   S.barrier_budget = (long long)(opt.barrier_timeout_ms * double(clk > 0 ? clk : 2000000));

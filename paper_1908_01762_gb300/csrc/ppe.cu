@@ -10,6 +10,7 @@
 #include <cooperative_groups.h>
 
 #include "sisph_internal.h"
+#include "ppe_sync.cuh"
 
 namespace sisph {
 
@@ -19,34 +20,6 @@ __device__ __forceinline__ void kahan_add(R &sum, R &comp, R v) {
   R t = sum + y;
   comp = (t - sum) - y;
   sum = t;
-}
-
-// ---------------------------------------------------------------------------
-// Stored PPE coefficients, one per ELL slot.  MIXED: the neighbour index and
-// the FP32 coefficient packed in 8 bytes, so that a sweep streams one array
-// with one load per slot; FP64: the coefficient alone (the index comes from
-// the neighbour list).
-// ---------------------------------------------------------------------------
-template <typename R>
-__device__ __forceinline__ void store_coef(void *base, long long o, int j, R fac) {
-  if constexpr (std::is_same<R, float>::value)
-    static_cast<uint2 *>(base)[o] = make_uint2(unsigned(j), __float_as_uint(fac));
-  else
-    static_cast<double *>(base)[o] = fac;
-}
-
-// Slot o of row i: neighbour j and coefficient (a slot past the row's end,
-// in[u] false, reads the row itself with a zero coefficient).
-template <typename R>
-__device__ __forceinline__ void load_coef(const State &S, long long o, bool in, int i, int &j, R &cf) {
-  if constexpr (std::is_same<R, float>::value) {
-    const uint2 v = in ? static_cast<const uint2 *>(S.coef)[o] : make_uint2(unsigned(i), 0u);
-    j = int(v.x);
-    cf = __uint_as_float(v.y);
-  } else {
-    j = in ? int(S.nbr[o] & kIdxMask) : i;
-    cf = in ? static_cast<const double *>(S.coef)[o] : 0.0;
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -113,6 +86,7 @@ __global__ void k_setup_fluid(State S) {
   DepSet deps{dtab, &dover};
   deps.init();
   double lam = 0.0;
+  bool inactive = false;
   if (i < t.end) {
     KC<R> K;
     K.set(P, P.h, P.inv_h, P.sig_h);
@@ -188,7 +162,11 @@ __global__ void k_setup_fluid(State S) {
       if constexpr (MX) S.pf[i] = 0.f;
     }
     if (active) lam = fabs(double(rhs) / double(dg));
+    inactive = !active;
   }
+  // free-surface (Dirichlet) rows per case: the BiCGStab solve needs one
+  const int ninact = __syncthreads_count(inactive);
+  if (threadIdx.x == 0 && ninact) atomicAdd(S.inact + t.c, ninact);
   deps.write(S, blockIdx.x, &dcnt);
   __shared__ double sh[32];
   for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
@@ -269,108 +247,6 @@ __global__ void k_setup_wall(State S) {
   deps.write(S, S.nft + blockIdx.x, &dcnt);
 }
 
-
-// ---------------------------------------------------------------------------
-// Grid barrier with a bounded wait.  All blocks are co-resident (cooperative
-// launch).  A wait that exceeds `budget` clock cycles, or that sees another
-// block's error, marks the error word and returns false; the caller returns.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ bool grid_sync(Barrier *b, unsigned nblocks, long long budget, bool skip_arrive) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ok = 1;
-    volatile unsigned *vgen = &b->gen;
-    volatile int *verr = &b->err;
-    unsigned g = *vgen;
-    __threadfence();
-    bool last = false;
-    if (!skip_arrive) last = (atomicAdd(&b->count, 1u) == nblocks - 1);
-    if (last) {
-      b->count = 0;
-      __threadfence();
-      atomicExch(&b->gen, g + 1u);
-    } else {
-      long long t0 = clock64();
-      while (*vgen == g) {
-        if (*verr) { ok = 0; break; }
-        if (clock64() - t0 > budget) {
-          atomicExch(&b->err, kErrTimeout);
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
-__device__ __forceinline__ void block_sum2f(float &a, float &b, double *sh) {
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-  }
-  int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  float *shf = reinterpret_cast<float *>(sh);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) { shf[w] = a; shf[32 + w] = b; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float sa = 0.f, sb = 0.f;
-    for (int q = 0; q < nw; ++q) { sa += shf[q]; sb += shf[32 + q]; }
-    a = sa;
-    b = sb;
-  }
-}
-
-__device__ __forceinline__ void block_sum2(double &a, double &b, double *sh) {
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-  }
-  int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) { sh[w] = a; sh[32 + w] = b; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double sa = 0.0, sb = 0.0;
-    for (int q = 0; q < nw; ++q) { sa += sh[q]; sb += sh[32 + q]; }
-    a = sa;
-    b = sb;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// One wall row of Eq. p-shepard: p_w = (sum_f p_f W_wf + H_w) / sum_f W_wf,
-// clamped at 0 in free-surface flows.  Chunks of 8: the index and weight
-// loads go out together, then the 8 pressure gathers.
-// ---------------------------------------------------------------------------
-template <typename R>
-__device__ __forceinline__ R wall_pressure(const State &S, const R *pc, int r, int w, int c) {
-  const R *wc = static_cast<const R *>(S.wcoef);
-  const long long nwl = S.nw;
-  R acc = static_cast<const R *>(S.wh)[r];
-  const int cnt = S.wcnt[r];
-  for (int q0 = 0; q0 < cnt; q0 += 8) {
-    int jj[8];
-    R ww[8];
-    _Pragma("unroll") for (int u = 0; u < 8; ++u) {
-      const int q = q0 + u;
-      const long long o = (long long)q * nwl + r;
-      jj[u] = q < cnt ? S.widx[o] : w;
-      ww[u] = q < cnt ? wc[o] : R(0);
-    }
-    R pv[8];
-    _Pragma("unroll") for (int u = 0; u < 8; ++u) pv[u] = pc[jj[u]];
-    _Pragma("unroll") for (int u = 0; u < 8; ++u) acc += ww[u] * pv[u];
-  }
-  R pw = acc * static_cast<const R *>(S.wsinv)[r];
-  if (S.cases[c].free_surface && pw < R(0)) pw = R(0);
-  return pw;
-}
 
 // One fluid row of Eq. p-sor: RHS_i + sum_j fac_ij p^k_j, in chunks of 8
 // slots (8 independent index/coefficient loads, then 8 independent
@@ -463,57 +339,6 @@ __device__ __forceinline__ int decide_case(const State &S, int c, int k, const d
   return stop_at;
 }
 
-// Exclusive prefix over the cases of a per-case count, in shared memory
-// (pre[0..nc], pre[nc] = total); thread t handles a contiguous run of
-// cases.  Returns the total.  Used to spread the work of the cases still
-// iterating evenly over the blocks.
-template <typename F>
-__device__ __forceinline__ int case_prefix(int nc, int *pre, int *wsum, F count) {
-  const int T = blockDim.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = T >> 5;
-  const int per = (nc + T - 1) / T;
-  const int c0 = threadIdx.x * per;
-  int sum = 0;
-  for (int c = c0; c < c0 + per && c < nc; ++c) sum += count(c);
-  int x = sum;
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) wsum[w] = x;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int a = 0;
-    for (int q = 0; q < nw; ++q) {
-      const int t = wsum[q];
-      wsum[q] = a;
-      a += t;
-    }
-    wsum[nw] = a;
-  }
-  __syncthreads();
-  int ex = wsum[w] + x - sum;
-  for (int c = c0; c < c0 + per && c < nc; ++c) {
-    pre[c] = ex;
-    ex += count(c);
-  }
-  if (threadIdx.x == 0) pre[nc] = wsum[nw];
-  __syncthreads();
-  const int total = pre[nc];
-  __syncthreads();
-  return total;
-}
-
-// The case c with pre[c] <= a < pre[c + 1] (pre non-decreasing).
-__device__ __forceinline__ int case_of_index(const int *pre, int nc, int a) {
-  int lo = 0, hi = nc - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (pre[mid] <= a) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
 // A case without fluid has nothing to solve; its solve still counts (one
 // block calls this).
 __device__ __forceinline__ void count_empty_solves(const State &S) {
@@ -540,11 +365,6 @@ __device__ __forceinline__ void count_empty_solves(const State &S) {
 // those reads after the other blocks' writes.  Flags and partial sums are
 // read with ld.global.cg.
 // ---------------------------------------------------------------------------
-// Up to this many cases the work of the cases still iterating is spread
-// evenly over the blocks in every phase; beyond, blocks stride over all
-// tiles and skip the finished ones.
-constexpr int kBalCases = 1024;
-
 template <bool MX>
 __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
   using R = typename std::conditional<MX, float, double>::type;
@@ -581,7 +401,7 @@ __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
       // (a case takes W phase k unless it stopped with fin < k sweeps)
       const int nrows = bal ? case_prefix(nc, apre, wsum, [&](int c) {
         const int f = __ldcg(fin + c);
-        return (k == 0 || f == 0 || f == k) ? S.cases[c].nw : 0;
+        return (jacobi_case(S, c) && (k == 0 || f == 0 || f == k)) ? S.cases[c].nw : 0;
       }) : S.nw;
       for (int a = blockIdx.x * T + threadIdx.x; a < nrows; a += nb * T) {
         int r = a;
@@ -591,7 +411,7 @@ __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
         }
         int w = S.wall_at[r];
         int c = S.case_of[w];
-        if (!bal && k > 0 && __ldcg(done + c) && __ldcg(fin + c) != k) continue;
+        if (!bal && (!jacobi_case(S, c) || (k > 0 && __ldcg(done + c) && __ldcg(fin + c) != k))) continue;
         R acc = wh[r];
         const int cnt = S.wcnt[r];
         for (int q0 = 0; q0 < cnt; q0 += 8) {
@@ -617,7 +437,8 @@ __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
     }
     // ---- any case left?  (a case without fluid has nothing to solve) ----
     int mine = 0;
-    for (int c = threadIdx.x; c < nc; c += T) mine |= (__ldcg(done + c) == 0 && S.cases[c].nf > 0);
+    for (int c = threadIdx.x; c < nc; c += T)
+      mine |= (__ldcg(done + c) == 0 && S.cases[c].nf > 0 && jacobi_case(S, c));
     if (!__syncthreads_or(mine)) break;
     if (k >= kcap) {
       if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(S.err, kErrNotConv);
@@ -632,7 +453,7 @@ __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
     const bool bal = nc <= kBalCases;
     const int ntiles = bal ? case_prefix(nc, apre, wsum, [&](int c) {
       const int f = __ldcg(fin + c);
-      return (f == 0 || f > k) ? S.cases[c].nftile : 0;
+      return (jacobi_case(S, c) && (f == 0 || f > k)) ? S.cases[c].nftile : 0;
     }) : S.nft;
     for (int a = blockIdx.x; a < ntiles; a += nb) {
       int tt = a;
@@ -641,7 +462,7 @@ __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
         tt = S.cases[c].ftile + (a - apre[c]);
       }
       const Tile &t = S.ftiles[tt];
-      if (!bal && __ldcg(done + t.c)) continue;
+      if (!bal && (__ldcg(done + t.c) || !jacobi_case(S, t.c))) continue;
       int i = t.beg + threadIdx.x;
       R dnr = R(0), dpr = R(0);
       if (i < t.end) {
@@ -696,6 +517,7 @@ __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
   // ---- publish the final pressure of every case ----
   for (int i = blockIdx.x * T + threadIdx.x; i < S.n; i += nb * T) {
     int c = S.case_of[i];
+    if (!jacobi_case(S, c)) continue;
     R v = __ldcg(static_cast<const R *>(S.pb[__ldcg(S.par + c)]) + i);
     S.p[i] = double(v);
     if constexpr (MX) S.pf[i] = v;
@@ -768,7 +590,9 @@ __device__ __forceinline__ int p2p_runs(const State &S, int c, int k, bool wall,
   if (threadIdx.x == 0) {
     int r = 1;
     const CaseDev &P = S.cases[c];
-    if (P.nf == 0) {
+    if (!jacobi_case(S, c)) {
+      r = 0;                                     // solved by BiCGStab
+    } else if (P.nf == 0) {
       r = (wall && k == 0) ? 1 : 0;             // nothing to solve: W(0) only
     } else {
       const int need = k - p2p_lag(k) + 1;       // decisions made
@@ -832,7 +656,7 @@ __device__ bool p2p_decide_loop(const State &S, double *sh, int *shv) {
     bool progress = false, left = false;
     for (int c = 0; c < nc; ++c) {
       const CaseDev &P = S.cases[c];
-      if (P.nf == 0) continue;
+      if (P.nf == 0 || !jacobi_case(S, c)) continue;
       if (threadIdx.x == 0) {
         int r = 0;       // 0: case done, 1: not ready, 2: decide sweep k
         if (!*reinterpret_cast<volatile const int *>(S.act + c)) {
@@ -968,7 +792,7 @@ __global__ void __launch_bounds__(256, MX ? 5 : 4) k_sweeps_p2p(State S) {
     for (int b = blockIdx.x; b < ntk; b += nb) {
       const Tile &t = kind ? S.wtiles[b] : S.ftiles[b];
       const int i = t.beg + threadIdx.x;
-      if (i >= t.end) continue;
+      if (i >= t.end || !jacobi_case(S, t.c)) continue;
       const R v = __ldcg(static_cast<const R *>(S.pb[__ldcg(S.par + t.c)]) + i);
       S.p[i] = double(v);
       if constexpr (MX) S.pf[i] = v;
@@ -977,6 +801,7 @@ __global__ void __launch_bounds__(256, MX ? 5 : 4) k_sweeps_p2p(State S) {
 }
 
 cudaError_t launch_ppe_setup(const State &S, const Launch &L) {
+  cudaMemsetAsync(S.inact, 0, sizeof(int) * size_t(S.ncases), L.stream);
   if (S.nft) {
     if (L.before) L.before(L.ctx, "ppe_setup");
     if (S.dim == 2) {
@@ -1014,14 +839,21 @@ int ppe_max_blocks_per_sm(const State &S, int block, bool p2p) {
   return nb;
 }
 
-cudaError_t launch_ppe_sweeps(const State &S, const Launch &L, int grid) {
+// Per-solve state shared by the BiCGStab and Jacobi launches (each touches
+// only its own cases' entries).
+cudaError_t launch_ppe_reset(const State &S, const Launch &L) {
   const size_t nc = size_t(S.ncases);
-  cudaMemsetAsync(S.bar, 0, sizeof(Barrier), L.stream);
-  // done[nc], fin[nc]; par[nc] and the arrival counters par[nc..3nc)
+  // done[nc], fin[nc]; par[nc] and the arrival counters par[nc..5nc)
   cudaMemsetAsync(S.act, 0, 2 * sizeof(int) * nc, L.stream);
   cudaMemsetAsync(S.par, 0, (1 + kRing) * sizeof(int) * nc, L.stream);
   cudaMemsetAsync(S.iters, 0, sizeof(int) * nc, L.stream);
   cudaMemsetAsync(S.pstat, 0, sizeof(int) * nc, L.stream);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ppe_sweeps(const State &S, const Launch &L, int grid) {
+  const size_t nc = size_t(S.ncases);
+  cudaMemsetAsync(S.bar, 0, sizeof(Barrier), L.stream);
   // point-to-point form when every block can own at most one fluid and one
   // wall tile (its per-tile waits would otherwise add up), unless forced; it
   // takes one more block, which makes the convergence decisions

@@ -45,6 +45,7 @@ struct CaseDev {
   int max_iter, pgrad_symm, free_surface, ustar_slip, pref_mode, K;
   double p_ref0;
   int adaptive;            // next dt from max|u^n|, max|f^n| (Sec. 3.2)
+  int solver;              // PPE: 0 damped Jacobi, 1 BiCGStab
   double dt_visc;          // 0.25 h^2 / nu (infinite without viscosity)
   // derived constants
   double cut2;             // (3h)^2, evaluated as (3*h)*(3*h)
@@ -142,6 +143,11 @@ struct State {
   int *deps, *ndeps;       // per tile: tiles its PPE rows read (kDepCap each)
   int *tflag;              // per tile: phases completed in this solve
   int *dsw;                // per case: convergence decisions made in this solve
+  // BiCGStab (only allocated when a case uses it)
+  int *inact;              // per case: free-surface rows of the last set-up
+  void *kv[6];             // r, r^, p, v, t, wall s (the sweep's precision)
+  double *kpart;           // per fluid tile: 4 partial sums
+  double *kscal;           // per case: 8 scalars
   // GTVF
   double *dg[2][3];        // FP64 displacement ping-pong
   float4 *dgf[2];          // FP32 displacement ping-pong
@@ -335,7 +341,11 @@ cudaError_t launch_scatter_disp(const State &S, const Launch &L, int comp, doubl
 cudaError_t launch_refresh_mirrors(const State &S, const Launch &L);
 // ppe.cu
 cudaError_t launch_ppe_setup(const State &S, const Launch &L);
+cudaError_t launch_ppe_reset(const State &S, const Launch &L);
 cudaError_t launch_ppe_sweeps(const State &S, const Launch &L, int grid);
+// krylov.cu
+cudaError_t launch_ppe_krylov(const State &S, const Launch &L, int grid);
+int krylov_max_blocks_per_sm(const State &S, int block);
 int ppe_max_blocks_per_sm(const State &S, int block, bool p2p);
 
 }  // namespace sisph

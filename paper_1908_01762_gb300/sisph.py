@@ -46,7 +46,7 @@ class sisph_case_params(C.Structure):
                 ("tol", C.c_double), ("max_iter", C.c_int32), ("pgrad_symm", C.c_int32),
                 ("free_surface", C.c_int32), ("ustar_slip", C.c_int32), ("pref_mode", C.c_int32),
                 ("p_ref", C.c_double), ("gtvf_hfac", C.c_double), ("gtvf_K", C.c_int32),
-                ("adaptive_dt", C.c_int32)]
+                ("adaptive_dt", C.c_int32), ("ppe_solver", C.c_int32)]
 
 
 class sisph_options(C.Structure):
@@ -174,6 +174,7 @@ def case_params_from_dict(prm):
     for key in ("max_iter", "pgrad_symm", "free_surface", "ustar_slip", "pref_mode", "gtvf_K"):
         setattr(q, key, int(prm[key]))
     q.adaptive_dt = int(prm.get("adaptive_dt", 0))
+    q.ppe_solver = int(prm.get("ppe_solver", 0))
     for k in range(3):
         q.g[k] = float(prm["g"][k])
     return q
