@@ -515,6 +515,56 @@ def study_tolerance(args):
             sim.close()
 
 
+def study_solver(args):
+    """Jacobi sweeps against BiCGStab on the same stored coefficients at equal
+    epsilon (the Krylov alternative of Sec. 3.1): iterations per step, time
+    per step and the pressure difference, one JSON line per run.  Free-surface
+    problems only (an enclosed or periodic flow's system is singular)."""
+    import torch
+    from paper_1908_01762_gb300 import sisph
+    import paper_1908_01762_gb300 as pkg
+    pkg.build()
+    problems = {
+        "dam_break_2d_dx0.004": lambda: workloads.dam_break_2d(dx=0.004),
+        "dam_break_2d_dx0.01": lambda: workloads.dam_break_2d(dx=0.01),
+        "dam_break_3d_dx0.016": lambda: workloads.dam_break_3d(dx=0.016),
+    }
+    for name, make in problems.items():
+        for tol in (1e-2, 1e-3, 1e-4, 1e-6):
+            res = {}
+            for solver in (0, 1):
+                case = make()
+                case["params"] = dict(case["params"], tol=tol, ppe_solver=solver)
+                sim = sisph.Simulation(case, precision=sisph.MIXED, use_graph=1)
+                try:
+                    sim.step(args.warmup)
+                    torch.cuda.synchronize()
+                    st0 = sim.stats()[0]
+                    t0 = time.perf_counter()
+                    for _ in range(args.steps):
+                        sim.step(1)
+                    torch.cuda.synchronize()
+                except sisph.SisphError as err:
+                    res[solver] = {"failed": str(err)}
+                    sim.close()
+                    continue
+                dt = time.perf_counter() - t0
+                st = sim.stats()[0]
+                res[solver] = {"iters_per_step": (st.total_iters - st0.total_iters) / args.steps,
+                               "ms_per_step": 1e3 * dt / args.steps, "p": sim.get("p"),
+                               "fluid": case["kind"] == 0}
+                sim.close()
+            out = {"study": "solver", "problem": name, "tol": tol, "steps": args.steps}
+            for solver, key in ((0, "jacobi"), (1, "bicgstab")):
+                r = res[solver]
+                out[key] = r if "failed" in r else {k: r[k] for k in ("iters_per_step", "ms_per_step")}
+            if "p" in res[0] and "p" in res[1]:
+                fl = res[0]["fluid"]
+                pj, pk = res[0]["p"][fl], res[1]["p"][fl]
+                out["p_rel_l2_difference"] = float(np.linalg.norm(pk - pj) / np.linalg.norm(pj))
+            print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -531,11 +581,14 @@ def main():
                          "look inside a graph with conditional nodes)")
     ap.add_argument("--roofline-kernel", default=None, choices=sorted(SITES),
                     help="time this site live instead of the dominant one (skips the site table)")
-    ap.add_argument("--study", choices=["tolerance"], default=None,
+    ap.add_argument("--study", choices=["tolerance", "solver"], default=None,
                     help="run a parameter study instead of the benchmark")
     args = ap.parse_args()
     if args.study == "tolerance":
         study_tolerance(args)
+        return
+    if args.study == "solver":
+        study_solver(args)
         return
     if args.warmup < 3:
         args.warmup = 3

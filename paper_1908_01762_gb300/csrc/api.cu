@@ -893,12 +893,12 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   int bps2 = ppe_max_blocks_per_sm(S, S.T, true);
   if (bps2 < 1) bps2 = 1;
   S.grid_cap_p2p = bps2 * nsm;
-  if (s->krylov) {
-    int bk = krylov_max_blocks_per_sm(S, S.T);
-    s->grid_k = std::max(1, std::min(s->grid, std::max(1, bk) * nsm));
-  }
   int want = std::max({S.nft, int((s->nw + S.T - 1) / S.T), ncases, 1});
   s->grid = std::min(want, bps * nsm);
+  if (s->krylov) {
+    int bk = krylov_max_blocks_per_sm(S, S.T);
+    s->grid_k = std::max(1, std::min(want, std::max(1, bk) * nsm));
+  }
   S.barrier_budget = (long long)(opt.barrier_timeout_ms * double(clk > 0 ? clk : 2000000));
 
   // first sort (places the walls for good), neighbour lists, wall normals
