@@ -568,7 +568,8 @@ def study_solver(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 200; 100 for c5)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2")
@@ -584,6 +585,11 @@ def main():
     ap.add_argument("--study", choices=["tolerance", "solver"], default=None,
                     help="run a parameter study instead of the benchmark")
     args = ap.parse_args()
+    if args.steps is None:
+        # the batch's high-Re Taylor-Green members start clustering after
+        # about 150 steps at eps = 1e-2 (the oracle does the same) and then
+        # overflow the neighbour capacity; every timed run starts at t = 0
+        args.steps = 100 if args.workload == "c5" else 200
     if args.study == "tolerance":
         study_tolerance(args)
         return

@@ -81,14 +81,21 @@ __device__ __forceinline__ const Tile &tile_of(const State &S, int b) {
   return b < S.nft ? S.ftiles[b] : S.wtiles[b - S.nft];
 }
 
-// A cell on the edge of a non-periodic grid holds the particles that left
-// the box (clamped into it), whose cell-relative coordinates can be large.
+// FP32 pair tests on cell-relative coordinates are trusted while both
+// coordinates lie within kNearCells cell widths of their cell's origin: every
+// operand of r_ij = rel_i - rel_j - o lc is then below 17 lc in magnitude, so
+// each component carries an absolute error below 34 * 2^-24 lc, and with lc
+// at most 8h (a skin of 3h in a periodic box of three cells) |r_ij|^2 near
+// the cutoff a relative error below 2e-5 of (3h)^2, inside the bands the
+// tests use.  Only a
+// particle that left a non-periodic box (clamped into an edge cell) can be
+// farther; its pairs take the FP64 test.
+constexpr float kNearCells = 8.0f;
 template <int DIM>
-__device__ __forceinline__ bool edge_cell(const CaseDev &P, const int c[3]) {
-  bool e = false;
-  _Pragma("unroll") for (int k = 0; k < DIM; ++k)
-    e |= !P.per[k] && (c[k] == 0 || c[k] == P.nc[k] - 1);
-  return e;
+__device__ __forceinline__ bool near_cell(const float4 &p, const float lc[3]) {
+  bool ok = fabsf(p.x) <= kNearCells * lc[0] && fabsf(p.y) <= kNearCells * lc[1];
+  if (DIM == 3) ok = ok && fabsf(p.z) <= kNearCells * lc[2];
+  return ok;
 }
 
 // FP32 position relative to the origin of the particle's rebuild cell (the
@@ -380,8 +387,8 @@ __global__ void k_copyback(State S, int gather_static) {
 // ---------------------------------------------------------------------------
 // rebuild: skin lists of the marked cases, every j within 3h + s of i (FP32
 // test on cell-relative coordinates with a relative margin of 2e-4 on the
-// squared cutoff, which covers its rounding; FP64 for pairs touching an edge
-// cell), all at the rebuild positions.  The list only has to contain N(i)
+// squared cutoff, which covers its rounding; FP64 for a pair with a particle
+// outside the near range), all at the rebuild positions.  The list only has to contain N(i)
 // at every later refresh before the next rebuild.
 // ---------------------------------------------------------------------------
 template <int DIM>
@@ -393,10 +400,11 @@ __global__ void __launch_bounds__(256) k_skin(State S) {
   const CaseDev &P = S.cases[t.c];
   int c[3];
   unpack_cell(S.cell[i], c);
-  const bool own_edge = edge_cell<DIM>(P, c);
   const double xi[3] = {S.xref[0][i], S.xref[1][i], DIM == 3 ? S.xref[2][i] : 0.0};
   const float4 pi = S.pf4[i];
-  const float lx = P.lcf[0], ly = P.lcf[1], lz = P.lcf[2];
+  const float lc[3] = {P.lcf[0], P.lcf[1], P.lcf[2]};
+  const float lx = lc[0], ly = lc[1], lz = lc[2];
+  const bool exact_all = !near_cell<DIM>(pi, lc);
   const float cut2f = float(P.cut_s2) * (1.0f + 2e-4f);
   const double cut2d = P.cut_s2 * (1.0 + 2e-4);
   const int zr = (DIM == 3) ? 1 : 0;
@@ -423,7 +431,6 @@ __global__ void __launch_bounds__(256) k_skin(State S) {
           cn[k] = v;
         }
         if (skip) continue;
-        const bool exact_all = own_edge || edge_cell<DIM>(P, cn);
         const unsigned code = stencil_code(ox, oy, oz) << kCodeShift;
         const float fx = pi.x - float(ox) * lx, fy = pi.y - float(oy) * ly, fz = pi.z - float(oz) * lz;
         const long long m = cell_key<DIM>(P, cn);
@@ -439,12 +446,17 @@ __global__ void __launch_bounds__(256) k_skin(State S) {
             continue;
           }
           // candidates 8 at a time: the loads go out together; slots past the
-          // cell's end get a far-away position and are rejected by the test
+          // cell's end get a far-away position and are rejected below
           for (unsigned j0 = beg; j0 < end; j0 += 8) {
             float4 pj[8];
             _Pragma("unroll") for (int u = 0; u < 8; ++u)
               pj[u] = j0 + u < end ? S.pf4[j0 + u] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
             _Pragma("unroll") for (int u = 0; u < 8; ++u) {
+              if (!near_cell<DIM>(pj[u], lc)) {
+                double d[3];
+                if (j0 + u < end && pair_d<DIM>(P, xi, S.xref, int(j0 + u), d) < cut2d) append((j0 + u) | code);
+                continue;
+              }
               float dx = fx - pj[u].x, dy = fy - pj[u].y;
               float r2f = dx * dx + dy * dy;
               if (DIM == 3) {
@@ -506,24 +518,29 @@ __global__ void k_sync(State S, int mode) {
 }
 
 // N(i) out of the skin list at the current positions: FP32 test on
-// cell-relative coordinates (error below 1e-5 of (3h)^2); a pair within a
-// relative band of 1e-4 of the cutoff is set aside and decided after the
-// loop by the exact unfused FP64 test, so the set equals the FP64 definition
-// and a warp pays for as many FP64 tests as its busiest lane (lattice inputs
-// put many pairs exactly on the cutoff).  Pairs touching an edge cell take
-// the FP64 test directly.  The list keeps the skin list's order.
+// cell-relative coordinates (error below 2e-5 of (3h)^2); a pair within a
+// relative band of 1e-4 of the cutoff, or with a particle outside the near
+// range, is set aside and decided after the loop by the exact unfused FP64
+// test, so the set equals the FP64 definition.  Lattice inputs put many pairs
+// exactly on the cutoff; their FP64 tests run from a register copy of the
+// case's periodic data, loaded once.  The order is deterministic: the skin
+// list's order, the set-aside pairs last.
+struct PeriodicBox {
+  int per[3];
+  double half[3], L[3];
+};
+
 template <int DIM>
-__global__ void __launch_bounds__(256) k_filter(State S) {
-  constexpr int kBand = DIM == 3 ? 48 : 16;
+__global__ void __launch_bounds__(256, 4) k_filter(State S) {
+  constexpr int kBand = DIM == 3 ? 48 : 16;   // at most 64 (one bit each below)
+  constexpr int kU = DIM == 3 ? 4 : 8;         // candidates whose loads go out together
   const Tile &t = tile_of(S, blockIdx.x);
   const int i = t.beg + threadIdx.x;
   if (i >= t.end) return;
   const CaseDev &P = S.cases[t.c];
-  int c[3];
-  unpack_cell(S.cell[i], c);
-  const bool own_edge = edge_cell<DIM>(P, c);
   const float4 pi = S.pf4[i];
   const float lc[3] = {P.lcf[0], P.lcf[1], P.lcf[2]};
+  const bool own_near = near_cell<DIM>(pi, lc);
   const float cut2f = float(P.cut2);
   const float lo_band = cut2f * (1.0f - 1e-4f), hi_band = cut2f * (1.0f + 1e-4f);
   const long long nn = S.n;
@@ -542,37 +559,53 @@ __global__ void __launch_bounds__(256) k_filter(State S) {
     double d[3];
     return pair_d<DIM>(P, xi, S.x, int(entry & kIdxMask), d) < P.cut2;
   };
-  for (int q0 = 0; q0 < scnt; q0 += 8) {
-    unsigned e[8];
-    _Pragma("unroll") for (int u = 0; u < 8; ++u)
-      e[u] = q0 + u < scnt ? S.snbr[(long long)(q0 + u) * nn + i] : (unsigned(i) | (stencil_code(0, 0, 0) << kCodeShift));
-    float4 pj[8];
-    _Pragma("unroll") for (int u = 0; u < 8; ++u) pj[u] = S.pf4[e[u] & kIdxMask];
-    _Pragma("unroll") for (int u = 0; u < 8; ++u) {
+  // the next chunk's entries are loaded while this chunk's positions are
+  // gathered (a slot past the row's end reads the row itself)
+  const unsigned self = unsigned(i) | (stencil_code(0, 0, 0) << kCodeShift);
+  unsigned en[kU];
+  _Pragma("unroll") for (int u = 0; u < kU; ++u) en[u] = u < scnt ? S.snbr[(long long)u * nn + i] : self;
+  for (int q0 = 0; q0 < scnt; q0 += kU) {
+    unsigned e[kU];
+    float4 pj[kU];
+    _Pragma("unroll") for (int u = 0; u < kU; ++u) {
+      e[u] = en[u];
+      pj[u] = S.pf4[e[u] & kIdxMask];
+    }
+    _Pragma("unroll") for (int u = 0; u < kU; ++u) {
+      const int q = q0 + kU + u;
+      en[u] = q < scnt ? S.snbr[(long long)q * nn + i] : self;
+    }
+    _Pragma("unroll") for (int u = 0; u < kU; ++u) {
       if (q0 + u >= scnt) continue;
-      const unsigned code = e[u] >> kCodeShift;
-      bool edge = own_edge;
-      if (!edge) {
-        const int cj[3] = {c[0] + int(code & 3u) - 1, c[1] + int((code >> 2) & 3u) - 1,
-                           c[2] + int(code >> 4) - 1};
-        edge = edge_cell<DIM>(P, cj);
-      }
-      if (edge) {
-        if (exact(e[u])) append(e[u]);
-        continue;
-      }
       float d[3];
-      const float r2f = pair_f<DIM>(lc, pi, pj[u], code, d);
-      if (r2f < lo_band) {
+      const float r2f = pair_f<DIM>(lc, pi, pj[u], e[u] >> kCodeShift, d);
+      const bool near = own_near && near_cell<DIM>(pj[u], lc);
+      if (near && r2f < lo_band) {
         append(e[u]);
-      } else if (r2f <= hi_band) {
+      } else if (!near || r2f <= hi_band) {
         if (nband < kBand) band[nband++] = e[u];
-        else if (exact(e[u])) append(e[u]);
+        else if (exact(e[u])) append(e[u]);     // a full band: decided here
       }
     }
   }
-  for (int b = 0; b < nband; ++b)
-    if (exact(band[b])) append(band[b]);
+  if (nband) {
+    PeriodicBox B;
+    _Pragma("unroll") for (int k = 0; k < 3; ++k) {
+      B.per[k] = P.per[k];
+      B.half[k] = P.half[k];
+      B.L[k] = P.L[k];
+    }
+    const double cut2 = P.cut2;
+    const double xi[3] = {S.x[0][i], S.x[1][i], DIM == 3 ? S.x[2][i] : 0.0};
+    // all tests first (no store between their loads), then the appends
+    unsigned long long keep = 0ull;
+    _Pragma("unroll 4") for (int b = 0; b < nband; ++b) {
+      double d[3];
+      keep |= (unsigned long long)(pair_d<DIM>(B, xi, S.x, int(band[b] & kIdxMask), d) < cut2) << b;
+    }
+    for (int b = 0; b < nband; ++b)
+      if ((keep >> b) & 1ull) append(band[b]);
+  }
   if (over) {
     atomicOr(S.err, kErrCapacity);
     cnt = S.cap;

@@ -223,9 +223,10 @@ __device__ __forceinline__ R sqrt_r(R v) {
 }
 
 // Minimum-image pair vector r_ij = r_i - r_j from FP64 positions, and
-// |r_ij|^2 = dx*dx + dy*dy (+ dz*dz) evaluated left to right, unfused.
-template <int DIM>
-__device__ __forceinline__ double pair_d(const CaseDev &P, const double xi[3],
+// |r_ij|^2 = dx*dx + dy*dy (+ dz*dz) evaluated left to right, unfused.  B is
+// a CaseDev or any type with its per/half/L members (a copy in registers).
+template <int DIM, class B>
+__device__ __forceinline__ double pair_d(const B &P, const double xi[3],
                                          double *const x[3], int j, double d[3]) {
 #pragma unroll
   for (int k = 0; k < DIM; ++k) {
@@ -279,17 +280,22 @@ __device__ __forceinline__ R divr(R a, R b) {
 // Rows in chunks of 8 slots: the 8 entries are loaded first and every slot
 // past the row's end is padded with the particle itself, so the gathers of a
 // chunk do not depend on branches and can all be in flight at once; `valid`
-// masks the padded slots out of the sums.
+// masks the padded slots out of the sums.  The next chunk's entries are
+// loaded while this chunk's gathers are in flight.
 #define ROW_CHUNKS(S, i, ...)                                                      \
   {                                                                                \
     const int _cnt = S.ncnt[i];                                                    \
     const long long _n = S.n;                                                      \
     const unsigned _self = unsigned(i) | (stencil_code(0, 0, 0) << kCodeShift);    \
+    unsigned _en[8];                                                               \
+    _Pragma("unroll") for (int _u = 0; _u < 8; ++_u)                              \
+      _en[_u] = _u < _cnt ? S.nbr[(long long)_u * _n + i] : _self;                \
     for (int _q0 = 0; _q0 < _cnt; _q0 += 8) {                                      \
       unsigned _e[8];                                                              \
       _Pragma("unroll") for (int _u = 0; _u < 8; ++_u) {                          \
-        const int _q = _q0 + _u;                                                   \
-        _e[_u] = _q < _cnt ? S.nbr[(long long)_q * _n + i] : _self;               \
+        _e[_u] = _en[_u];                                                          \
+        const int _q = _q0 + 8 + _u;                                               \
+        _en[_u] = _q < _cnt ? S.nbr[(long long)_q * _n + i] : _self;              \
       }                                                                            \
       _Pragma("unroll") for (int _u = 0; _u < 8; ++_u) {                          \
         const unsigned e = _e[_u];                                                 \
