@@ -8,6 +8,11 @@
  * with the CUDA library.
  *
  * Readings of passages that the paper leaves open are marked "Reading:".
+ * Parity unpinned: the slip ghost velocity used for u* (or_ghost_velocity,
+ * slip form), the 1e-6 length below which a smoothed wall normal is zero
+ * (or_wall_normals) and the artificial-viscosity form (Monaghan's, read from
+ * a garbled equation) have no value of their own to be checked against; the
+ * hydrostatic, cavity and dam-break tests only exercise them.
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared.
  */
 #include "sisph_oracle.h"

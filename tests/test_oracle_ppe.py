@@ -10,6 +10,8 @@ coeff1, p-sor, convergence; Sec. 3.4, Eq. p-shepard).
 * average iteration counts sit in the paper's "typically 2-10" range at the
   paper's tolerance (Table 1).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -163,18 +165,34 @@ def test_jacobi_fixed_point_equals_lu(oracle_lib):
     assert np.max(np.abs(p[fluid] - sol)) < 1e-9 * scale
 
 
-def test_iteration_counts_in_paper_range(oracle_lib):
-    # Table 1: about 2 iterations per step at eps = 1e-2 (dam break, cavity)
+def _table_iterations():
+    """Table 1 of the paper (average Jacobi iterations per step), from
+    tests/golden/jacobi_iterations_table.txt: {(problem, tol): iterations}."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "jacobi_iterations_table.txt")
+    out = {}
+    for line in open(path):
+        line = line.split("#", 1)[0].split()
+        if line:
+            out[(line[0], float(line[1]))] = float(line[2])
+    return out
+
+
+def test_iteration_counts_match_table_1(oracle_lib):
+    table = _table_iterations()
+    # dam break at eps = 1e-2: the printed 2.0 (min_iter) at every step
     db = workloads.dam_break_2d(dx=0.02)
     s = oracle.Sim(db, tol=1e-2)
     rc, ds = s.step(10)
     its = [d.iters for d in ds]
-    assert 2 <= np.mean(its) <= 10
+    assert abs(np.mean(its) - table[("dam_break_2d", 0.01)]) < 0.25
+    # cavity at eps = 1e-2: the run starts from rest, so its first steps take
+    # more sweeps than the whole-run average of the table; after the start-up
+    # the count settles within a few times the printed value
     ldc = workloads.lid_driven_cavity(30)
     s = oracle.Sim(ldc, tol=1e-2)
     rc, ds = s.step(40)
     its = [d.iters for d in ds[20:]]
-    assert 2 <= np.mean(its) <= 10
+    assert table[("cavity", 0.01)] <= np.mean(its) <= 5 * table[("cavity", 0.01)]
     assert min(d.iters for d in ds) >= 2   # min_iter = 2 (Listing 1)
 
 
