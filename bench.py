@@ -6,13 +6,14 @@ tolerance, pressure gradient, GTVF, update) over the whole particle set.
 
 Default workload: the perturbed 400 x 400 Taylor-Green vortex (160,000
 particles, dx = 0.0025, +-0.05 dx seeded noise, Re = 100, h = dx, PPE
-tolerance 1e-4, asymm gradient, p_ref = 100) in the MIXED form (FP32 sums and
-sweeps, FP64 residual and integration), replayed from a CUDA graph.
+tolerance 1e-4, asymm gradient, p_ref = 2 max p after the first solve) in
+the MIXED form (FP32 sums and sweeps, FP64 residual and integration),
+replayed from a CUDA graph.
 Timed steps are bracketed by CUDA events on the library's stream, with a
 256 MiB buffer written between steps to flush the 126 MiB L2.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload c1|c2|c3|c4|c5] [--precision mixed|fp64]
+                    [--workload c1|c2|c3|c4|c4l|c5] [--precision mixed|fp64]
 
 With N > 1 (torchrun) every rank runs its own replica ("replicas only": one
 case does not shard without a halo exchange); the line reports the total
@@ -55,6 +56,9 @@ def make_workload(name):
     if name == "c4":
         return [workloads.dam_break_3d(dx=0.008)], \
             "dam_break_3d: 0.55x1.0x0.55 m column in 1.6x1.0x0.6 m tank, dx 0.008, 3 wall layers"
+    if name == "c4l":
+        return [workloads.dam_break_3d(dx=0.00524)], \
+            "dam_break_3d_large: 0.55x1.0x0.55 m column in 1.6x1.0x0.6 m tank, dx 0.00524, 3 wall layers"
     if name == "c5":
         return workloads.batch_ensemble(64), \
             "batch64: 32 TGV (Re 50-1000) + 32 cavity (Re 100-1000), n_side 50-300, ~2.5M"
@@ -71,24 +75,28 @@ SITES = {"check": "nbr.cu", "sort": "nbr.cu", "build": "nbr.cu", "sync": "nbr.cu
          "update": "passes.cu", "speed_max": "passes.cu", "adapt_dt": "passes.cu"}
 
 
-def measured_traffic(workload, site):
-    """DRAM bytes per launch of one kernel from the committed ncu summary
-    profiles/<site>_<workload>_traffic.md, or None if there is none or the
+def measured_traffic(workload, site, per_launch_bytes):
+    """DRAM bytes (read + write) per launch of one kernel, from the committed
+    ncu summary profiles/<site>_<workload>_traffic.md: the DRAM bytes of the
+    captured launch per algorithmic byte of that launch, times this run's
+    algorithmic bytes per launch (a captured solve may take more or fewer
+    sweeps than the average one).  None if there is no summary or the
     kernel's source file changed since the counters were taken."""
     import hashlib
     path = os.path.join(ROOT, "profiles", f"{site}_{workload}_traffic.md")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or not per_launch_bytes:
         return None
     vals = {}
     for line in open(path):
-        if ":" in line and line.split(":")[0].strip() in ("traffic_per_launch_bytes", "kernel_source_sha1"):
+        if ":" in line and line.split(":")[0].strip() in ("dram_bytes_per_algorithmic_byte",
+                                                          "kernel_source_sha1"):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
     src = os.path.join(ROOT, "paper_1908_01762_gb300", "csrc", SITES[site])
     sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
-    if vals.get("kernel_source_sha1") != sha or "traffic_per_launch_bytes" not in vals:
+    if vals.get("kernel_source_sha1") != sha or "dram_bytes_per_algorithmic_byte" not in vals:
         return None
-    return float(vals["traffic_per_launch_bytes"])
+    return float(vals["dram_bytes_per_algorithmic_byte"]) * per_launch_bytes
 
 
 def measured_hbm_peak():
@@ -364,7 +372,7 @@ def run_ours(args, rank, world):
         "roofline": {"kernel": roof_site, "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
-                     "traffic": measured_traffic(args.workload, roof_site), "peak_source": peak_kind,
+                     "traffic": measured_traffic(args.workload, roof_site, per_launch_bytes), "peak_source": peak_kind,
                      "bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms,
                      "launches": nk,
                      "share_of_step": (kern_ms / t_ms) if t_ms else None},

@@ -684,6 +684,7 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   A(&S.ncnt, N);
   A(&S.snbr, N * size_t(S.scap));
   A(&S.sncnt, N);
+  A(&S.wfin, N);
   A(&S.cell, N);
   A(&S.bcell, N);
   A(&S.need, ncases);
@@ -873,6 +874,7 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   if (e == cudaSuccess) e = cudaMemset(S.pstat, 0, ncases * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(S.err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(S.bar, 0, sizeof(Barrier));
+  if (e == cudaSuccess) e = cudaMemset(S.wfin, 0, sizeof(int) * N);
   for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMemset(S.vgt[k], 0, N * sizeof(double));
   for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
     if (S.mixed) e = cudaMemset(S.dgf[p], 0, N * sizeof(float4));

@@ -388,8 +388,13 @@ __global__ void k_copyback(State S, int gather_static) {
 // rebuild: skin lists of the marked cases, every j within 3h + s of i (FP32
 // test on cell-relative coordinates with a relative margin of 2e-4 on the
 // squared cutoff, which covers its rounding; FP64 for a pair with a particle
-// outside the near range), all at the rebuild positions.  The list only has to contain N(i)
-// at every later refresh before the next rebuild.
+// outside the near range), all at the rebuild positions.  The list only has
+// to contain N(i) at every later refresh before the next rebuild.
+// Walls never move, so the wall-wall pairs of a wall row are final here: a
+// wall row starts with its wall neighbours within 3h exactly (the filter's
+// FP32 test with the FP64 decision inside the band), wfin[i] of them, then
+// its fluid skin candidates.  The refresh copies that head unchanged, and the
+// wall passes, which sum over fluid neighbours only, start after it.
 // ---------------------------------------------------------------------------
 template <int DIM>
 __global__ void __launch_bounds__(256) k_skin(State S) {
@@ -398,6 +403,7 @@ __global__ void __launch_bounds__(256) k_skin(State S) {
   const int i = t.beg + threadIdx.x;
   if (i >= t.end) return;
   const CaseDev &P = S.cases[t.c];
+  const bool wall_row = i >= P.wbeg;
   int c[3];
   unpack_cell(S.cell[i], c);
   const double xi[3] = {S.xref[0][i], S.xref[1][i], DIM == 3 ? S.xref[2][i] : 0.0};
@@ -407,6 +413,8 @@ __global__ void __launch_bounds__(256) k_skin(State S) {
   const bool exact_all = !near_cell<DIM>(pi, lc);
   const float cut2f = float(P.cut_s2) * (1.0f + 2e-4f);
   const double cut2d = P.cut_s2 * (1.0 + 2e-4);
+  const float cutf = float(P.cut2);
+  const float lo_band = cutf * (1.0f - 1e-4f), hi_band = cutf * (1.0f + 1e-4f);
   const int zr = (DIM == 3) ? 1 : 0;
   const long long nn = S.n;
   int cnt = 0;
@@ -416,65 +424,88 @@ __global__ void __launch_bounds__(256) k_skin(State S) {
     else over = true;
     ++cnt;
   };
-  for (int oz = -zr; oz <= zr; ++oz) {
-    for (int oy = -1; oy <= 1; ++oy) {
-      for (int ox = -1; ox <= 1; ++ox) {
-        const int o[3] = {ox, oy, oz};
-        int cn[3] = {c[0], c[1], c[2]};
-        bool skip = false;
-        _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
-          int v = c[k] + o[k];
-          if (v < 0 || v >= P.nc[k]) {
-            if (P.per[k]) v = (v + P.nc[k]) % P.nc[k];
-            else skip = true;
-          }
-          cn[k] = v;
-        }
-        if (skip) continue;
-        const unsigned code = stencil_code(ox, oy, oz) << kCodeShift;
-        const float fx = pi.x - float(ox) * lx, fy = pi.y - float(oy) * ly, fz = pi.z - float(oz) * lz;
-        const long long m = cell_key<DIM>(P, cn);
-        for (int kind = 0; kind < 2; ++kind) {
-          if (kind == 1 && P.nw == 0) break;
-          const long long q = P.key_base + (long long)kind * P.slots + m;
-          const unsigned beg = S.hist[q], end = S.hist[q + 1];
-          if (exact_all) {
-            for (unsigned j = beg; j < end; ++j) {
-              double d[3];
-              if (pair_d<DIM>(P, xi, S.xref, int(j), d) < cut2d) append(j | code);
+  // candidates of the stencil cells in buckets k0..k1 (0 fluid, 1 walls);
+  // exact: N(i) itself (3h, walls only), else the skin test (3h + s)
+  auto scan = [&](int k0, int k1, bool exact) {
+    const double cut_d = exact ? P.cut2 : cut2d;
+    for (int oz = -zr; oz <= zr; ++oz) {
+      for (int oy = -1; oy <= 1; ++oy) {
+        for (int ox = -1; ox <= 1; ++ox) {
+          const int o[3] = {ox, oy, oz};
+          int cn[3] = {c[0], c[1], c[2]};
+          bool skip = false;
+          _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
+            int v = c[k] + o[k];
+            if (v < 0 || v >= P.nc[k]) {
+              if (P.per[k]) v = (v + P.nc[k]) % P.nc[k];
+              else skip = true;
             }
-            continue;
+            cn[k] = v;
           }
-          // candidates 8 at a time: the loads go out together; slots past the
-          // cell's end get a far-away position and are rejected below
-          for (unsigned j0 = beg; j0 < end; j0 += 8) {
-            float4 pj[8];
-            _Pragma("unroll") for (int u = 0; u < 8; ++u)
-              pj[u] = j0 + u < end ? S.pf4[j0 + u] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
-            _Pragma("unroll") for (int u = 0; u < 8; ++u) {
-              if (!near_cell<DIM>(pj[u], lc)) {
+          if (skip) continue;
+          const unsigned code = stencil_code(ox, oy, oz) << kCodeShift;
+          const float fx = pi.x - float(ox) * lx, fy = pi.y - float(oy) * ly, fz = pi.z - float(oz) * lz;
+          const long long m = cell_key<DIM>(P, cn);
+          for (int kind = k0; kind <= k1; ++kind) {
+            if (kind == 1 && P.nw == 0) break;
+            const long long q = P.key_base + (long long)kind * P.slots + m;
+            const unsigned beg = S.hist[q], end = S.hist[q + 1];
+            if (exact_all) {
+              for (unsigned j = beg; j < end; ++j) {
                 double d[3];
-                if (j0 + u < end && pair_d<DIM>(P, xi, S.xref, int(j0 + u), d) < cut2d) append((j0 + u) | code);
-                continue;
+                if (pair_d<DIM>(P, xi, S.xref, int(j), d) < cut_d) append(j | code);
               }
-              float dx = fx - pj[u].x, dy = fy - pj[u].y;
-              float r2f = dx * dx + dy * dy;
-              if (DIM == 3) {
-                float dz = fz - pj[u].z;
-                r2f += dz * dz;
+              continue;
+            }
+            // candidates 8 at a time: the loads go out together; slots past
+            // the cell's end get a far-away position and are rejected below
+            for (unsigned j0 = beg; j0 < end; j0 += 8) {
+              float4 pj[8];
+              _Pragma("unroll") for (int u = 0; u < 8; ++u)
+                pj[u] = j0 + u < end ? S.pf4[j0 + u] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
+              _Pragma("unroll") for (int u = 0; u < 8; ++u) {
+                const unsigned j = j0 + u;
+                if (!near_cell<DIM>(pj[u], lc)) {
+                  double d[3];
+                  if (j < end && pair_d<DIM>(P, xi, S.xref, int(j), d) < cut_d) append(j | code);
+                  continue;
+                }
+                float dx = fx - pj[u].x, dy = fy - pj[u].y;
+                float r2f = dx * dx + dy * dy;
+                if (DIM == 3) {
+                  float dz = fz - pj[u].z;
+                  r2f += dz * dz;
+                }
+                if (!exact) {
+                  if (r2f < cut2f) append(j | code);
+                } else if (r2f < lo_band) {
+                  append(j | code);
+                } else if (r2f <= hi_band) {
+                  double d[3];
+                  if (pair_d<DIM>(P, xi, S.xref, int(j), d) < P.cut2) append(j | code);
+                }
               }
-              if (r2f < cut2f) append((j0 + u) | code);
             }
           }
         }
       }
     }
+  };
+  int head = 0;
+  if (wall_row) {
+    scan(1, 1, true);
+    head = cnt;
+    scan(0, 0, false);
+  } else {
+    scan(0, 1, false);
   }
   if (over) {
     atomicOr(S.err, kErrCapacity);
     cnt = S.scap;
+    head = min(head, S.scap);
   }
   S.sncnt[i] = cnt;
+  S.wfin[i] = head;
 }
 
 // ---------------------------------------------------------------------------
@@ -523,8 +554,9 @@ __global__ void k_sync(State S, int mode) {
 // range, is set aside and decided after the loop by the exact unfused FP64
 // test, so the set equals the FP64 definition.  Lattice inputs put many pairs
 // exactly on the cutoff; their FP64 tests run from a register copy of the
-// case's periodic data, loaded once.  The order is deterministic: the skin
-// list's order, the set-aside pairs last.
+// case's periodic data, loaded once.  A wall row's head (its wall neighbours,
+// decided at the rebuild) is copied first.  The order is deterministic: the
+// skin list's order, the set-aside pairs last.
 struct PeriodicBox {
   int per[3];
   double half[3], L[3];
@@ -545,6 +577,7 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
   const float lo_band = cut2f * (1.0f - 1e-4f), hi_band = cut2f * (1.0f + 1e-4f);
   const long long nn = S.n;
   const int scnt = S.sncnt[i];
+  const int head = S.wfin[i];
   int cnt = 0;
   bool over = false;
   unsigned band[kBand];
@@ -559,12 +592,20 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
     double d[3];
     return pair_d<DIM>(P, xi, S.x, int(entry & kIdxMask), d) < P.cut2;
   };
+  // a wall row's head (its wall neighbours, decided at the rebuild) is final
+  for (int q0 = 0; q0 < head; q0 += 4) {
+    unsigned h4[4];
+    _Pragma("unroll") for (int u = 0; u < 4; ++u)
+      h4[u] = q0 + u < head ? S.snbr[(long long)(q0 + u) * nn + i] : 0u;
+    _Pragma("unroll") for (int u = 0; u < 4; ++u)
+      if (q0 + u < head) append(h4[u]);
+  }
   // the next chunk's entries are loaded while this chunk's positions are
   // gathered (a slot past the row's end reads the row itself)
   const unsigned self = unsigned(i) | (stencil_code(0, 0, 0) << kCodeShift);
   unsigned en[kU];
-  _Pragma("unroll") for (int u = 0; u < kU; ++u) en[u] = u < scnt ? S.snbr[(long long)u * nn + i] : self;
-  for (int q0 = 0; q0 < scnt; q0 += kU) {
+  _Pragma("unroll") for (int u = 0; u < kU; ++u) en[u] = head + u < scnt ? S.snbr[(long long)(head + u) * nn + i] : self;
+  for (int q0 = head; q0 < scnt; q0 += kU) {
     unsigned e[kU];
     float4 pj[kU];
     _Pragma("unroll") for (int u = 0; u < kU; ++u) {

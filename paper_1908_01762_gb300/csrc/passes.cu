@@ -66,12 +66,13 @@ __device__ __forceinline__ void tvel(const State &S, int j, R u[3]) {
   }
 }
 
-#define ROW_LOOP(S, i, ...)                                   \
+#define ROW_LOOP(S, i, ...) ROW_LOOP_FROM(S, i, 0, __VA_ARGS__)
+#define ROW_LOOP_FROM(S, i, k0, ...)                          \
   {                                                            \
     const int _cnt = S.ncnt[i];                                \
     const long long _n = S.n;                                  \
     _Pragma("unroll 4")                                        \
-    for (int _k = 0; _k < _cnt; ++_k) {                        \
+    for (int _k = (k0); _k < _cnt; ++_k) {                     \
       const unsigned e = S.nbr[(long long)_k * _n + i];        \
       __VA_ARGS__                                              \
     }                                                          \
@@ -168,7 +169,8 @@ __global__ void k_ghost(State S, int slip_stage) {
   G.init(S, i);
   R sw = R(0), su[3] = {R(0), R(0), R(0)};
   const int fend = P.fbeg + P.nf;
-  ROW_LOOP(S, i, {
+  // fluid neighbours only: they follow the row's wall head
+  ROW_LOOP_FROM(S, i, S.wfin[i], {
     int j = int(e & kIdxMask);
     if (j < fend) {
       R d[3];

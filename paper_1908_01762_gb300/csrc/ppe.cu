@@ -204,29 +204,43 @@ __device__ __forceinline__ void wall_row(const State &S, const Tile &t, int i, D
   const int cnti = S.ncnt[i];
   const long long n = S.n, nw = S.nw;
   R *wc = static_cast<R *>(S.wcoef);
-  for (int k = 0; k < cnti; ++k) {
-    unsigned e = S.nbr[(long long)k * n + i];
-    int j = int(e & kIdxMask);
-    if (j >= fend) continue;
-    R d[3], r2, rj;
+  // fluid neighbours only: they follow the row's wall head.  Chunks of 8:
+  // the entries, then the gathers, go out together before any store.
+  const unsigned self = unsigned(i) | (stencil_code(0, 0, 0) << kCodeShift);
+  for (int q0 = S.wfin[i]; q0 < cnti; q0 += 8) {
+    unsigned e[8];
+    _Pragma("unroll") for (int u = 0; u < 8; ++u) e[u] = q0 + u < cnti ? S.nbr[(long long)(q0 + u) * n + i] : self;
+    float4 pj[8];
+    float rjf[8];
     if constexpr (MX) {
-      float4 pj = S.pf4[j];
-      r2 = pair_f<DIM>(K.lc, pi4, pj, e >> kCodeShift, d);
-      rj = S.vf4[j].w;
-    } else {
-      double dd[3];
-      r2 = pair_d<DIM>(P, xi, S.x, j, dd);
-      _Pragma("unroll") for (int q = 0; q < DIM; ++q) d[q] = dd[q];
-      if (DIM == 2) d[2] = 0.0;
-      rj = S.rho[j];
+      _Pragma("unroll") for (int u = 0; u < 8; ++u) {
+        const int j = int(e[u] & kIdxMask);
+        pj[u] = S.pf4[j];
+        rjf[u] = S.vf4[j].w;
+      }
     }
-    R w = K.sig * poly_w<R>(qof<R>(sqrt_r(r2), K.h, K.ih));
-    deps.insert(S.tile_of[j]);
-    S.widx[(long long)cnt * nw + r] = j;
-    wc[(long long)cnt * nw + r] = w;
-    ++cnt;
-    sw += w;
-    _Pragma("unroll") for (int q = 0; q < DIM; ++q) acc[q] += rj * d[q] * w;
+    _Pragma("unroll") for (int u = 0; u < 8; ++u) {
+      const int j = int(e[u] & kIdxMask);
+      if (q0 + u >= cnti || j >= fend) continue;
+      R d[3], r2, rj;
+      if constexpr (MX) {
+        r2 = pair_f<DIM>(K.lc, pi4, pj[u], e[u] >> kCodeShift, d);
+        rj = rjf[u];
+      } else {
+        double dd[3];
+        r2 = pair_d<DIM>(P, xi, S.x, j, dd);
+        _Pragma("unroll") for (int q = 0; q < DIM; ++q) d[q] = dd[q];
+        if (DIM == 2) d[2] = 0.0;
+        rj = S.rho[j];
+      }
+      R w = K.sig * poly_w<R>(qof<R>(sqrt_r(r2), K.h, K.ih));
+      deps.insert(S.tile_of[j]);
+      S.widx[(long long)cnt * nw + r] = j;
+      wc[(long long)cnt * nw + r] = w;
+      ++cnt;
+      sw += w;
+      _Pragma("unroll") for (int q = 0; q < DIM; ++q) acc[q] += rj * d[q] * w;
+    }
   }
   R hw = R(0);
   _Pragma("unroll") for (int q = 0; q < DIM; ++q) hw += R(P.g[q]) * acc[q];

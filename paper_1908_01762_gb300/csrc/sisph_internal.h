@@ -109,6 +109,7 @@ struct State {
   int *ncnt;
   unsigned *snbr;          // skin lists, same layout, capacity scap
   int *sncnt;
+  int *wfin;               // wall rows: leading wall entries, final at the rebuild
   int *need;               // per case: rebuild at this refresh
   int *anyneed;            // some case needs a rebuild
   int *force;              // next refresh rebuilds every case: 1 at the
