@@ -392,9 +392,10 @@ __global__ void k_copyback(State S, int gather_static) {
 // to contain N(i) at every later refresh before the next rebuild.
 // Walls never move, so the wall-wall pairs of a wall row are final here: a
 // wall row starts with its wall neighbours within 3h exactly (the filter's
-// FP32 test with the FP64 decision inside the band), wfin[i] of them, then
-// its fluid skin candidates.  The refresh copies that head unchanged, and the
-// wall passes, which sum over fluid neighbours only, start after it.
+// FP32 test with the FP64 decision inside the band), wfin[i] of them, built
+// at forced rebuilds only, then its fluid skin candidates.  The refresh
+// copies that head unchanged, and the wall passes, which sum over fluid
+// neighbours only, start after it.
 // ---------------------------------------------------------------------------
 template <int DIM>
 __global__ void __launch_bounds__(256) k_skin(State S) {
@@ -492,7 +493,13 @@ __global__ void __launch_bounds__(256) k_skin(State S) {
     }
   };
   int head = 0;
-  if (wall_row) {
+  if (wall_row && *S.force == 0) {
+    // walls keep their positions, cells and sorted order between rebuilds
+    // that nothing forced (creation, a caller's sisph_set and a restore all
+    // force one), so the head built last time is still in place
+    head = cnt = S.wfin[i];
+    scan(0, 0, false);
+  } else if (wall_row) {
     scan(1, 1, true);
     head = cnt;
     scan(0, 0, false);
