@@ -1,0 +1,53 @@
+"""Host-side pieces of bench.py: the algorithmic byte models of the roofline
+and the reading of the committed ncu traffic summaries (no GPU needed)."""
+import glob
+import hashlib
+import os
+
+import numpy as np
+import pytest
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_sweep_bytes_per_row_and_wall():
+    # MIXED (4-byte values): 8 bytes per slot (index + coefficient) and 20 per
+    # fluid row (RHS, omega/D, count, p read, p written); 8 per wall entry and
+    # 16 per wall row (count, 1/S, H, p_w)
+    counts = np.full(10, 29)
+    fluid, walls = bench.sweep_bytes(counts, 3, np.array([12, 12, 12]), 4)
+    assert fluid == 10 * (8 * 29 + 20)
+    assert walls == 3 * 12 * 8 + 3 * 16
+    # FP64: 12 bytes per slot (4-byte index from the list, 8-byte coefficient)
+    fluid, walls = bench.sweep_bytes(counts, 0, np.zeros(0), 8)
+    assert fluid == 10 * (12 * 29 + 36) and walls == 0
+
+
+def test_filter_bytes():
+    # per particle 32 bytes, per skin entry 4 read, per kept entry 4 written
+    assert bench.kernel_bytes("filter", True, 3, 7, 10, 50, 60, 90) == 10 * 32 + 4 * 90 + 4 * 60
+    assert bench.kernel_bytes("no_such_site", True, 3, 1, 1, 1, 1, 1) is None
+
+
+@pytest.mark.parametrize("path", sorted(glob.glob(os.path.join(ROOT, "profiles", "*_traffic.md"))))
+def test_traffic_summaries_are_read_only_for_the_kernel_they_measured(path):
+    name = os.path.basename(path)[:-len("_traffic.md")]
+    site, workload = name.rsplit("_", 1)
+    assert site in bench.SITES
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    ratio = float(vals["dram_bytes_per_algorithmic_byte"])
+    assert ratio > 0
+    src = os.path.join(ROOT, "paper_1908_01762_gb300", "csrc", bench.SITES[site])
+    current = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    got = bench.measured_traffic(workload, site, 1.0e9)
+    if vals["kernel_source_sha1"] == current:
+        assert got == pytest.approx(ratio * 1.0e9)
+    else:
+        assert got is None        # the kernel changed since the counters were taken
+    assert bench.measured_traffic(workload, site, 0.0) is None
