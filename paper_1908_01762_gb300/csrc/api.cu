@@ -895,6 +895,10 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   int bps2 = ppe_max_blocks_per_sm(S, S.T, true);
   if (bps2 < 1) bps2 = 1;
   S.grid_cap_p2p = bps2 * nsm;
+  {
+    const int tiles = std::max(S.nft, S.nwt);
+    S.p2p = (S.ppe_sync == 2 || (S.ppe_sync == 0 && S.grid_cap_p2p >= tiles + 1)) ? 1 : 0;
+  }
   int want = std::max({S.nft, int((s->nw + S.T - 1) / S.T), ncases, 1});
   s->grid = std::min(want, bps * nsm);
   if (s->krylov) {

@@ -25,9 +25,9 @@ __device__ __forceinline__ void kahan_add(R &sum, R &comp, R v) {
 // ---------------------------------------------------------------------------
 // Tile dependencies of the point-to-point sweeps: the set of other tiles
 // whose rows a tile's PPE rows read, collected in a shared-memory hash set
-// while the rows are set up, then written as a list (ndeps = -1 when the
-// list would exceed kDepCap or the set overflows: the tile then waits for
-// every tile of its case).
+// while the rows are set up (only when the handle's sweeps take that form),
+// then written as a list (ndeps = -1 when the list would exceed kDepCap or
+// the set overflows: the tile then waits for every tile of its case).
 // ---------------------------------------------------------------------------
 constexpr int kHash = 512;
 
@@ -143,7 +143,7 @@ __global__ void k_setup_fluid(State S) {
       }
       if (valid) {
         store_coef<R>(S.coef, (long long)k * _n + i, j, fac);
-        if (j != i) {
+        if (S.p2p && j != i) {
           const int dt = S.tile_of[j];
           if (dt != int(blockIdx.x)) deps.insert(dt);
         }
@@ -167,7 +167,7 @@ __global__ void k_setup_fluid(State S) {
   // free-surface (Dirichlet) rows per case: the BiCGStab solve needs one
   const int ninact = __syncthreads_count(inactive);
   if (threadIdx.x == 0 && ninact) atomicAdd(S.inact + t.c, ninact);
-  deps.write(S, blockIdx.x, &dcnt);
+  if (S.p2p) deps.write(S, blockIdx.x, &dcnt);
   __shared__ double sh[32];
   for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = lam;
@@ -234,7 +234,7 @@ __device__ __forceinline__ void wall_row(const State &S, const Tile &t, int i, D
         rj = S.rho[j];
       }
       R w = K.sig * poly_w<R>(qof<R>(sqrt_r(r2), K.h, K.ih));
-      deps.insert(S.tile_of[j]);
+      if (S.p2p) deps.insert(S.tile_of[j]);
       S.widx[(long long)cnt * nw + r] = j;
       wc[(long long)cnt * nw + r] = w;
       ++cnt;
@@ -258,7 +258,7 @@ __global__ void k_setup_wall(State S) {
   DepSet deps{dtab, &dover};
   deps.init();
   if (i < t.end) wall_row<DIM, MX>(S, t, i, deps);
-  deps.write(S, S.nft + blockIdx.x, &dcnt);
+  if (S.p2p) deps.write(S, S.nft + blockIdx.x, &dcnt);
 }
 
 
@@ -872,7 +872,7 @@ cudaError_t launch_ppe_sweeps(const State &S, const Launch &L, int grid) {
   // wall tile (its per-tile waits would otherwise add up), unless forced; it
   // takes one more block, which makes the convergence decisions
   const int tiles = S.nft > S.nwt ? S.nft : S.nwt;
-  const bool p2p = S.ppe_sync == 2 || (S.ppe_sync == 0 && S.grid_cap_p2p >= tiles + 1);
+  const bool p2p = S.p2p != 0;
   if (p2p) grid = (tiles + 1 < S.grid_cap_p2p ? tiles + 1 : S.grid_cap_p2p);
   if (p2p && grid < 2) grid = 2;
   if (p2p) {

@@ -139,6 +139,7 @@ struct State {
   int *err;
   // point-to-point PPE sweeps (tiles numbered: fluid tiles, then wall tiles)
   int ppe_sync;            // 0 auto, 1 grid barrier per phase, 2 per-tile flags
+  int p2p;                 // the sweeps take the per-tile flag form (set-up collects tile dependencies)
   int grid_cap_p2p;        // co-resident blocks of the point-to-point form
   const int *tile_of;      // sorted index -> tile
   int *deps, *ndeps;       // per tile: tiles its PPE rows read (kDepCap each)
