@@ -344,6 +344,7 @@ def run_ours(args, rank, world):
         per_launch_bytes = kernel_bytes(roof_site, mixed, dim, n_fluid, n, float(np.sum(counts[fl])),
                                         float(np.sum(counts)), float(np.sum(nskin)))
     avg_ms = kern_ms / nk if nk else float("nan")
+    traffic = measured_traffic(args.workload, roof_site, per_launch_bytes)
     achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9 if nk else None
     peak, peak_kind = measured_hbm_peak()
     rebuilds = np.array([s.rebuilds for s in sim.stats()]) - rb0
@@ -372,7 +373,8 @@ def run_ours(args, rank, world):
         "roofline": {"kernel": roof_site, "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
-                     "traffic": measured_traffic(args.workload, roof_site, per_launch_bytes), "peak_source": peak_kind,
+                     "traffic": traffic, "peak_source": peak_kind,
+                     "dram_achieved": (traffic / (avg_ms * 1e-3) / 1e9) if (traffic and nk) else None,
                      "bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms,
                      "launches": nk,
                      "share_of_step": (kern_ms / t_ms) if t_ms else None},
@@ -486,8 +488,7 @@ def study_tolerance(args):
     from paper_1908_01762_gb300 import sisph
     import paper_1908_01762_gb300 as pkg
     pkg.build()
-    # the 400 x 400 TGV: coarser TGV lattices are above the stability limit of
-    # the GTVF update at p_ref = 100 (see the design notes)
+    # the benchmark's 400 x 400 TGV, a 100 x 100 cavity and the 2D dam break
     problems = {
         "tgv400_re100": lambda tol: workloads.taylor_green(400, perturb=0.05, tol=tol),
         "cavity100_re100": lambda tol: workloads.lid_driven_cavity(100, tol=tol),
@@ -521,6 +522,76 @@ def study_tolerance(args):
                 out["decay_rate_exact"] = -8 * math.pi ** 2 / 100.0
             print(json.dumps(out), flush=True)
             sim.close()
+
+
+def _timed_steps(sim, steps, warmup=3):
+    """ms per step of `steps` steps after `warmup` untimed ones (device synced)."""
+    import torch
+    for _ in range(warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sim.step(1)
+    torch.cuda.synchronize()
+    return 1e3 * (time.perf_counter() - t0) / steps
+
+
+def study_batch(args):
+    """The batch of 64 cases (C5) in one handle against the same cases run one
+    after another on handles of their own, MIXED and FP64: milliseconds per
+    step of the whole batch, one JSON line."""
+    from paper_1908_01762_gb300 import sisph
+    import paper_1908_01762_gb300 as pkg
+    pkg.build()
+    cases = workloads.batch_ensemble(64)
+    out = {"study": "batch", "cases": len(cases), "n": int(sum(c["n"] for c in cases)),
+           "steps": args.steps}
+    sim = sisph.Simulation(cases, precision=sisph.MIXED, use_graph=1)
+    out["batched_mixed_ms_per_step"] = _timed_steps(sim, args.steps)
+    sim.close()
+    for prec, key in ((sisph.MIXED, "sequential_mixed_ms_per_step"), (sisph.FP64, "sequential_fp64_ms_per_step")):
+        tot = 0.0
+        for c in cases:
+            sim = sisph.Simulation(c, precision=prec, use_graph=1)
+            tot += _timed_steps(sim, args.steps)
+            sim.close()
+        out[key] = tot
+    print(json.dumps(out), flush=True)
+
+
+def study_eisph(args):
+    """EISPH (one Jacobi sweep per step) against SISPH on the Taylor-Green
+    vortex at Re = 10^4, 100 x 100 particles perturbed by up to dx/10 (Sec.
+    4.2): velocity error against the exact decay after `steps` steps."""
+    from paper_1908_01762_gb300 import sisph
+    import paper_1908_01762_gb300 as pkg
+    pkg.build()
+    for name, tol, max_iter, min_iter in (("sisph", 1e-2, 1000, 2), ("eisph", 0.0, 1, 1)):
+        case = workloads.taylor_green(100, re=1e4, perturb=0.1, seed=1908, tol=tol)
+        case["params"] = dict(case["params"], max_iter=max_iter)
+        sim = sisph.Simulation(case, precision=sisph.FP64, use_graph=1, min_iter=min_iter)
+        out = {"study": "eisph", "scheme": name, "re": 1e4, "n_side": 100, "tol": tol,
+               "steps": args.steps}
+        try:
+            for _ in range(args.steps):
+                rc = sim.step(1)
+        except sisph.SisphError as err:
+            out["failed"] = str(err)
+            print(json.dumps(out), flush=True)
+            sim.close()
+            continue
+        t = args.steps * case["params"]["dt"]
+        x, y, u, v = sim.get("x"), sim.get("y"), sim.get("u"), sim.get("v")
+        ue, ve, _ = workloads.tgv_exact(x, y, t, re=1e4)
+        speed = np.sqrt(u * u + v * v)
+        out["t"] = t
+        out["max_speed"] = float(speed.max())
+        out["max_speed_exact"] = float(math.exp(-8 * math.pi ** 2 / 1e4 * t))
+        out["velocity_l1_error"] = float(np.mean(np.hypot(u - ue, v - ve)) / np.mean(np.hypot(ue, ve)))
+        out["sweeps_per_step"] = sim.stats()[0].total_iters / max(1, sim.stats()[0].solves)
+        print(json.dumps(out), flush=True)
+        sim.close()
 
 
 def study_solver(args):
@@ -590,7 +661,7 @@ def main():
                          "look inside a graph with conditional nodes)")
     ap.add_argument("--roofline-kernel", default=None, choices=sorted(SITES),
                     help="time this site live instead of the dominant one (skips the site table)")
-    ap.add_argument("--study", choices=["tolerance", "solver"], default=None,
+    ap.add_argument("--study", choices=["tolerance", "solver", "batch", "eisph"], default=None,
                     help="run a parameter study instead of the benchmark")
     args = ap.parse_args()
     if args.steps is None:
@@ -603,6 +674,12 @@ def main():
         return
     if args.study == "solver":
         study_solver(args)
+        return
+    if args.study == "batch":
+        study_batch(args)
+        return
+    if args.study == "eisph":
+        study_eisph(args)
         return
     if args.warmup < 3:
         args.warmup = 3
