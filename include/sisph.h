@@ -192,13 +192,18 @@ void sisph_destroy(sisph_t s);
  * (3h)^2}, minimum image, exactly.  A case whose fluid moved more than s/2
  * since its last rebuild (every case, after sisph_set of a position) is first
  * sorted into Morton-ordered cells and gets new skin lists; then every list is
- * filtered from its skin list.  sisph_step does this twice per step; call it
- * after sisph_set of a position before using the lists outside a step. */
+ * filtered from its skin list.  sisph_step does this twice per step, leaving
+ * out the pairs within a relative 4e-5 of the cutoff (|r_ij| > 3h(1 - 3e-5),
+ * where the kernel's weight and gradient are below FP64 rounding of every
+ * sum); call it after sisph_set of a position before using the lists outside
+ * a step. */
 int sisph_build_neighbors(sisph_t s);
 
-/* Neighbour lists in the caller's order: counts[n] and, if idx is not NULL,
- * the lists concatenated with caller indices in ascending order (capacity
- * idx_cap entries).  *total receives the number of pairs. */
+/* Neighbour lists N(i) at the current positions, exactly (the lists are
+ * first brought there as by sisph_build_neighbors), in the caller's order:
+ * counts[n] and, if idx is not NULL, the lists concatenated with caller
+ * indices in ascending order (capacity idx_cap entries).  *total receives the
+ * number of pairs. */
 int sisph_neighbors(sisph_t s, int32_t *counts, int32_t *idx, int64_t idx_cap, int64_t *total);
 
 /* Summation density (Eq. summation_density) at the current neighbour lists. */

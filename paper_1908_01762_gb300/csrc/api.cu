@@ -256,7 +256,7 @@ cudaError_t capture_rebuild_conditional(sisph_t s, int mode, bool first) {
 // the device: in a captured step by a conditional node (unless a profiled
 // site lies in the group, whose kernels then return at once without a
 // rebuild), in direct launches by reading the decision back.
-cudaError_t do_refresh(sisph_t s, int mode, bool first) {
+cudaError_t do_refresh(sisph_t s, int mode, bool first, bool exact = false) {
   Launch L = mk_launch(s);
   cudaError_t e = launch_refresh_check(s->S, L, mode);
   if (e != cudaSuccess) return e;
@@ -272,7 +272,7 @@ cudaError_t do_refresh(sisph_t s, int mode, bool first) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e == cudaSuccess && any) e = launch_refresh_rebuild(s->S, L, mode, first, false);
   }
-  if (e == cudaSuccess) e = launch_refresh_finish(s->S, L, mode);
+  if (e == cudaSuccess) e = launch_refresh_finish(s->S, L, mode, exact);
   return e;
 }
 
@@ -909,7 +909,7 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
 
   // first sort (places the walls for good), neighbour lists, wall normals
   e = force_rebuild(s);
-  if (e == cudaSuccess) e = do_refresh(s, 0, true);
+  if (e == cudaSuccess) e = do_refresh(s, 0, true, true);
   if (e == cudaSuccess) e = launch_normals(S, mk_launch(s));
   if (e != cudaSuccess) {
     int rc = cuda_fail(nullptr, e, "initial neighbour build");
@@ -958,7 +958,7 @@ void sisph_destroy(sisph_t s) {
 
 int sisph_build_neighbors(sisph_t s) {
   if (!valid_handle(s)) return fail(s, SISPH_EINVAL, "invalid handle");
-  cudaError_t e = do_refresh(s, 0, false);
+  cudaError_t e = do_refresh(s, 0, false, true);
   if (e != cudaSuccess) return cuda_fail(s, e, "build_neighbors");
   return check_status(s, false);
 }
@@ -1131,7 +1131,13 @@ int sisph_neighbors(sisph_t s, int32_t *counts, int32_t *idx, int64_t idx_cap, i
   const size_t N = size_t(s->n);
   std::vector<int> cnt(N), uid(N);
   std::vector<unsigned> nbr(N * size_t(s->S.cap));
-  cudaError_t e = cudaStreamSynchronize(s->stream);
+  // the exact lists at the current positions (a step's own refreshes leave
+  // out the pairs at the rim of the support)
+  cudaError_t e = do_refresh(s, 0, false, true);
+  if (e != cudaSuccess) return cuda_fail(s, e, "neighbors");
+  const int rc = check_status(s, false);
+  if (rc != SISPH_OK) return rc;
+  e = cudaStreamSynchronize(s->stream);
   if (e == cudaSuccess) e = cudaMemcpy(cnt.data(), s->S.ncnt, N * sizeof(int), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(uid.data(), s->S.uid, N * sizeof(int), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && idx)

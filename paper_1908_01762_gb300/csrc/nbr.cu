@@ -556,20 +556,29 @@ __global__ void k_sync(State S, int mode) {
 }
 
 // N(i) out of the skin list at the current positions: FP32 test on
-// cell-relative coordinates (error below 2e-5 of (3h)^2); a pair within a
-// relative band of 1e-4 of the cutoff, or with a particle outside the near
-// range, is set aside and decided after the loop by the exact unfused FP64
-// test, so the set equals the FP64 definition.  Lattice inputs put many pairs
-// exactly on the cutoff; their FP64 tests run from a register copy of the
-// case's periodic data, loaded once.  A wall row's head (its wall neighbours,
-// decided at the rebuild) is copied first.  The order is deterministic: the
-// skin list's order, the set-aside pairs last.
+// cell-relative coordinates (error below 2e-5 of (3h)^2).
+//   EXACT (the lists the API shows): a pair within a relative band of 1e-4 of
+//     the cutoff, or with a particle outside the near range, is set aside and
+//     decided after the loop by the exact unfused FP64 test, so the set equals
+//     the FP64 definition.  Lattice inputs put many pairs exactly on the
+//     cutoff; their FP64 tests run from a register copy of the case's
+//     periodic data, loaded once.
+//   otherwise (the refreshes inside a step): fluid rows leave out the pairs
+//     whose FP32 |r_ij|^2 is within a relative 4e-5 below the cutoff or
+//     above it, so no FP64 test runs unless a particle is outside the near
+//     range.  Every pair left out has |r_ij| > 3h (1 - 3e-5), where the
+//     quintic's weight is below 1e-21 and its gradient below 1e-17 of their
+//     largest values, so no sum of a fluid row changes above FP64 rounding.
+//     Wall rows, whose Shepard sums are normalised, stay exact.
+// A wall row's head (its wall neighbours, decided exactly at the rebuild) is
+// copied first.  The order is deterministic: the skin list's order, the
+// set-aside pairs last.
 struct PeriodicBox {
   int per[3];
   double half[3], L[3];
 };
 
-template <int DIM>
+template <int DIM, bool EXACT>
 __global__ void __launch_bounds__(256, 4) k_filter(State S) {
   constexpr int kBand = DIM == 3 ? 48 : 16;   // at most 64 (one bit each below)
   constexpr int kU = DIM == 3 ? 4 : 8;         // candidates whose loads go out together
@@ -581,7 +590,10 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
   const float lc[3] = {P.lcf[0], P.lcf[1], P.lcf[2]};
   const bool own_near = near_cell<DIM>(pi, lc);
   const float cut2f = float(P.cut2);
-  const float lo_band = cut2f * (1.0f - 1e-4f), hi_band = cut2f * (1.0f + 1e-4f);
+  // wall rows stay exact: their Shepard sums are normalised, so a wall whose
+  // only fluid neighbour sits on the rim takes that neighbour's value
+  const bool ex = EXACT || blockIdx.x >= unsigned(S.nft);
+  const float lo_band = cut2f * (ex ? 1.0f - 1e-4f : 1.0f - 4e-5f), hi_band = cut2f * (1.0f + 1e-4f);
   const long long nn = S.n;
   const int scnt = S.sncnt[i];
   const int head = S.wfin[i];
@@ -630,13 +642,16 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
       const bool near = own_near && near_cell<DIM>(pj[u], lc);
       if (near && r2f < lo_band) {
         append(e[u]);
-      } else if (!near || r2f <= hi_band) {
+      } else if (!near) {
+        if (ex && nband < kBand) band[nband++] = e[u];
+        else if (exact(e[u])) append(e[u]);
+      } else if (ex && r2f <= hi_band) {
         if (nband < kBand) band[nband++] = e[u];
         else if (exact(e[u])) append(e[u]);     // a full band: decided here
       }
     }
   }
-  if (nband) {
+  if (ex && nband) {
     PeriodicBox B;
     _Pragma("unroll") for (int k = 0; k < 3; ++k) {
       B.per[k] = P.per[k];
@@ -723,7 +738,7 @@ cudaError_t launch_refresh_rebuild(const State &S, const Launch &L, int mode, bo
   return cudaGetLastError();
 }
 
-cudaError_t launch_refresh_finish(const State &S, const Launch &L, int mode) {
+cudaError_t launch_refresh_finish(const State &S, const Launch &L, int mode, bool exact) {
   const int nt = S.nft + S.nwt;
   const int nb = (S.n + 255) / 256;
   if (L.before) L.before(L.ctx, "sync");
@@ -731,8 +746,13 @@ cudaError_t launch_refresh_finish(const State &S, const Launch &L, int mode) {
   else k_sync<3><<<nb, 256, 0, L.stream>>>(S, mode);
   if (L.after) L.after(L.ctx, "sync", double(S.n), 1);
   if (L.before) L.before(L.ctx, "filter");
-  if (S.dim == 2) k_filter<2><<<nt, S.T, 0, L.stream>>>(S);
-  else k_filter<3><<<nt, S.T, 0, L.stream>>>(S);
+  if (exact) {
+    if (S.dim == 2) k_filter<2, true><<<nt, S.T, 0, L.stream>>>(S);
+    else k_filter<3, true><<<nt, S.T, 0, L.stream>>>(S);
+  } else {
+    if (S.dim == 2) k_filter<2, false><<<nt, S.T, 0, L.stream>>>(S);
+    else k_filter<3, false><<<nt, S.T, 0, L.stream>>>(S);
+  }
   if (L.after) L.after(L.ctx, "filter", double(S.n), 1);
   cudaMemsetAsync(S.force, 0, sizeof(int), L.stream);
   return cudaGetLastError();

@@ -327,7 +327,7 @@ struct Launch {
 cudaError_t launch_refresh_check(const State &S, const Launch &L, int mode);
 cudaError_t launch_refresh_rebuild(const State &S, const Launch &L, int mode, bool gather_static,
                                    bool count_on_device);
-cudaError_t launch_refresh_finish(const State &S, const Launch &L, int mode);
+cudaError_t launch_refresh_finish(const State &S, const Launch &L, int mode, bool exact);
 cudaError_t launch_set_conditional(const State &S, const Launch &L, cudaGraphConditionalHandle h);
 constexpr int kRebuildKernels = 10;   // kernels of launch_refresh_rebuild
 // passes.cu
