@@ -537,6 +537,45 @@ def _timed_steps(sim, steps, warmup=3):
     return 1e3 * (time.perf_counter() - t0) / steps
 
 
+def step_log(args, path):
+    """Per-step record of a replica run of the workload, one JSON line per
+    step: PPE sweeps, final residual and Lambda per case, max |u|, neighbour
+    count min / mean / max, and PPE interactions per second of the step."""
+    import torch
+    from paper_1908_01762_gb300 import sisph
+    cases, _ = make_workload(args.workload)
+    prec = sisph.MIXED if args.precision == "mixed" else sisph.FP64
+    sim = sisph.Simulation(cases, precision=prec, use_graph=1)
+    stream = torch.cuda.current_stream()
+    sisph.sisph_set_stream(sim.h, stream.cuda_stream)
+    dim = cases[0]["dim"]
+    comps = ("u", "v", "w")[:dim]
+    offs = np.cumsum([0] + [c["n"] for c in cases])
+    fl = np.concatenate([c["kind"] for c in cases]) == 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with open(path, "w") as f:
+        for k in range(args.steps):
+            e0.record(stream)
+            sim.step(1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            st = sim.stats()
+            counts, _ = sim.neighbors()
+            speed = np.sqrt(sum(sim.get(c) ** 2 for c in comps))[fl]   # walls hold ghost velocities
+            iters = [int(x.iters) for x in st]
+            # PPE interactions: fluid rows' neighbours times their case's sweeps
+            pairs = float(sum(it * np.sum(counts[a:b][fl[a:b]]) for it, a, b in zip(iters, offs[:-1], offs[1:])))
+            rec = {"step": k, "ms": ms, "time": [float(x.time) for x in st],
+                   "ppe_sweeps": iters, "residual": [float(x.residual) for x in st],
+                   "lambda": [float(x.lambda_) for x in st], "max_speed": float(speed.max()),
+                   "neighbours": {"min": int(counts.min()), "mean": float(counts.mean()),
+                                  "max": int(counts.max())},
+                   "ppe_interactions_per_s": pairs / (ms * 1e-3)}
+            f.write(json.dumps(rec) + "\n")
+    sim.close()
+
+
 def study_batch(args):
     """The batch of 64 cases (C5) in one handle against the same cases run one
     after another on handles of their own, MIXED and FP64: milliseconds per
@@ -661,6 +700,9 @@ def main():
                          "look inside a graph with conditional nodes)")
     ap.add_argument("--roofline-kernel", default=None, choices=sorted(SITES),
                     help="time this site live instead of the dominant one (skips the site table)")
+    ap.add_argument("--log", default=None,
+                    help="also write a per-step JSONL record (sweeps, residual, Lambda, max |u|, "
+                         "neighbour counts) of a replica run to this file")
     ap.add_argument("--study", choices=["tolerance", "solver", "batch", "eisph"], default=None,
                     help="run a parameter study instead of the benchmark")
     args = ap.parse_args()
@@ -696,6 +738,8 @@ def main():
     out = run_ours(args, rank, world)
     if rank == 0:
         print(json.dumps(out))
+        if args.log:
+            step_log(args, args.log)
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()

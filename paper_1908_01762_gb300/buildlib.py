@@ -11,6 +11,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsisph.so")
+# with every gathered neighbour index bounds-checked on the device
+# (SISPH_CHECKED: a bad index raises SISPH_EINTERNAL instead of being read)
+CHECKED_LIB = os.path.join(PKG, "libsisph_checked.so")
 SOURCES = ["nbr.cu", "passes.cu", "ppe.cu", "krylov.cu", "api.cu", "noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "sisph_internal.h"), os.path.join(CSRC, "ppe_sync.cuh"),
            os.path.join(ROOT, "include", "sisph.h")]
@@ -33,17 +36,21 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every translation unit (in parallel) and link libsisph.so."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile every translation unit (in parallel) and link libsisph.so
+    (libsisph_checked.so with checked=True)."""
+    bdir = os.path.join(BUILD, "checked") if checked else BUILD
+    lib = CHECKED_LIB if checked else LIB
+    flags = FLAGS + (["-DSISPH_CHECKED"] if checked else [])
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(bdir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + HEADERS):
-            jobs.append([nvcc, *FLAGS, *ARCH, "-c", s, "-o", o])
+            jobs.append([nvcc, *flags, *ARCH, "-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -55,11 +62,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
             list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -1,8 +1,10 @@
 // Host runtime behind the C-ABI of include/sisph.h: validation, the static
 // particle layout, device allocation, the order of the kernels in one time
 // step (Algorithm 1), CUDA-graph capture and replay, event timing, field
-// access in the caller's order, and checkpoints.
+// access in the caller's order, and checkpoints.  Every kernel site and API
+// call is an NVTX range (header-only NVTX 3: inert unless a tool attaches).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -115,8 +117,17 @@ bool profiled(sisph_t s, const char *name) {
   return false;
 }
 
+// An NVTX range around one API call.
+struct NvtxScope {
+  explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+  ~NvtxScope() { nvtxRangePop(); }
+  NvtxScope(const NvtxScope &) = delete;
+  NvtxScope &operator=(const NvtxScope &) = delete;
+};
+
 void before_cb(void *ctx, const char *name) {
   sisph_t s = static_cast<sisph_t>(ctx);
+  nvtxRangePushA(name);
   if (!profiled(s, name)) return;
   if (s->capturing) {
     // a dedicated pair per launch site, recorded as external event nodes
@@ -151,6 +162,7 @@ void before_cb(void *ctx, const char *name) {
 
 void after_cb(void *ctx, const char *name, double units, int nk) {
   sisph_t s = static_cast<sisph_t>(ctx);
+  nvtxRangePop();
   if (s->counting) s->launches += nk;
   if (!profiled(s, name)) return;
   if (s->capturing) {
@@ -337,6 +349,8 @@ int check_status(sisph_t s, bool sweeps_ran) {
   if (err & kErrCapacity)
     return fail(s, SISPH_ECAPACITY, "a particle has more neighbours than the neighbour capacity");
   if (err & kErrNonFinite) return fail(s, SISPH_ENONFINITE, "non-finite PPE residual");
+  if (err & kErrInternal)
+    return fail(s, SISPH_EINTERNAL, "checked build: a gathered neighbour index was out of range");
   if (err & kErrNotConv) return fail(s, SISPH_ENOTCONVERGED, "PPE reached max_iter before the tolerance");
   return SISPH_OK;
 }
@@ -504,6 +518,7 @@ const char *sisph_last_error(sisph_t s) { return s ? s->err.c_str() : g_create_e
 
 int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph_case_params *params,
                        const sisph_options *opt_in, sisph_t *out) {
+  NvtxScope nvtx("sisph_batch_create");
   if (!out) return fail(nullptr, SISPH_EINVAL, "out is NULL");
   *out = nullptr;
   if (ncases <= 0 || !parts || !params) return fail(nullptr, SISPH_EINVAL, "no cases");
@@ -957,6 +972,7 @@ void sisph_destroy(sisph_t s) {
 }
 
 int sisph_build_neighbors(sisph_t s) {
+  NvtxScope nvtx("sisph_build_neighbors");
   if (!valid_handle(s)) return fail(s, SISPH_EINVAL, "invalid handle");
   cudaError_t e = do_refresh(s, 0, false, true);
   if (e != cudaSuccess) return cuda_fail(s, e, "build_neighbors");
@@ -964,6 +980,7 @@ int sisph_build_neighbors(sisph_t s) {
 }
 
 int sisph_compute_density(sisph_t s) {
+  NvtxScope nvtx("sisph_compute_density");
   if (!valid_handle(s)) return fail(s, SISPH_EINVAL, "invalid handle");
   cudaError_t e = launch_density(s->S, mk_launch(s));
   if (e != cudaSuccess) return cuda_fail(s, e, "density");
@@ -971,6 +988,7 @@ int sisph_compute_density(sisph_t s) {
 }
 
 int sisph_ppe_solve(sisph_t s, double tol, int32_t max_iter, int32_t *iters, double *residual) {
+  NvtxScope nvtx("sisph_ppe_solve");
   if (!valid_handle(s)) return fail(s, SISPH_EINVAL, "invalid handle");
   if (max_iter < 1 || !(tol >= 0.0)) return fail(s, SISPH_EINVAL, "max_iter >= 1 and tol >= 0 required");
   // the solve's tolerance and cap on top of the device copy of the cases
@@ -1005,6 +1023,7 @@ int sisph_ppe_solve(sisph_t s, double tol, int32_t max_iter, int32_t *iters, dou
 }
 
 int sisph_step(sisph_t s, int32_t nsteps) {
+  NvtxScope nvtx("sisph_step");
   if (!valid_handle(s)) return fail(s, SISPH_EINVAL, "invalid handle");
   if (nsteps < 0) return fail(s, SISPH_EINVAL, "nsteps must be >= 0");
   bool use_graph = s->opt.use_graph && !(s->profiling && s->prof_only.empty()) && !s->graph_failed;
@@ -1289,6 +1308,7 @@ static int copy_in(sisph_t s, const double *host, double *dst) {
 }
 
 int sisph_save(sisph_t s, const char *path) {
+  NvtxScope nvtx("sisph_save");
   if (!valid_handle(s) || !path) return fail(s, SISPH_EINVAL, "invalid handle or path");
   FILE *f = fopen(path, "wb");
   if (!f) return fail(s, SISPH_EINVAL, std::string("cannot open ") + path);
@@ -1330,6 +1350,7 @@ int sisph_save(sisph_t s, const char *path) {
 }
 
 int sisph_load(sisph_t s, const char *path) {
+  NvtxScope nvtx("sisph_load");
   if (!valid_handle(s) || !path) return fail(s, SISPH_EINVAL, "invalid handle or path");
   FILE *f = fopen(path, "rb");
   if (!f) return fail(s, SISPH_EINVAL, std::string("cannot open ") + path);

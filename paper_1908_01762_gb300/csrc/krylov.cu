@@ -71,6 +71,7 @@ __device__ __forceinline__ R wall_linear(const State &S, const R *a, const R *b,
       const long long o = (long long)q * nwl + r;
       jj[u] = q < cnt ? S.widx[o] : w;
       ww[u] = q < cnt ? wc[o] : R(0);
+      SISPH_CHECK_IDX(S, jj[u], w);
     }
     _Pragma("unroll") for (int u = 0; u < 8; ++u) {
       const R val = b ? a[jj[u]] - al * b[jj[u]] : a[jj[u]];

@@ -616,8 +616,10 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
     unsigned h4[4];
     _Pragma("unroll") for (int u = 0; u < 4; ++u)
       h4[u] = q0 + u < head ? S.snbr[(long long)(q0 + u) * nn + i] : 0u;
-    _Pragma("unroll") for (int u = 0; u < 4; ++u)
+    _Pragma("unroll") for (int u = 0; u < 4; ++u) {
+      SISPH_CHECK_ENTRY(S, h4[u], unsigned(i));
       if (q0 + u < head) append(h4[u]);
+    }
   }
   // the next chunk's entries are loaded while this chunk's positions are
   // gathered (a slot past the row's end reads the row itself)
@@ -629,6 +631,7 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
     float4 pj[kU];
     _Pragma("unroll") for (int u = 0; u < kU; ++u) {
       e[u] = en[u];
+      SISPH_CHECK_ENTRY(S, e[u], self);
       pj[u] = S.pf4[e[u] & kIdxMask];
     }
     _Pragma("unroll") for (int u = 0; u < kU; ++u) {

@@ -73,7 +73,8 @@ __device__ __forceinline__ void tvel(const State &S, int j, R u[3]) {
     const long long _n = S.n;                                  \
     _Pragma("unroll 4")                                        \
     for (int _k = (k0); _k < _cnt; ++_k) {                     \
-      const unsigned e = S.nbr[(long long)_k * _n + i];        \
+      unsigned e = S.nbr[(long long)_k * _n + i];              \
+      SISPH_CHECK_ENTRY(S, e, unsigned(i));                    \
       __VA_ARGS__                                              \
     }                                                          \
   }

@@ -209,7 +209,10 @@ __device__ __forceinline__ void wall_row(const State &S, const Tile &t, int i, D
   const unsigned self = unsigned(i) | (stencil_code(0, 0, 0) << kCodeShift);
   for (int q0 = S.wfin[i]; q0 < cnti; q0 += 8) {
     unsigned e[8];
-    _Pragma("unroll") for (int u = 0; u < 8; ++u) e[u] = q0 + u < cnti ? S.nbr[(long long)(q0 + u) * n + i] : self;
+    _Pragma("unroll") for (int u = 0; u < 8; ++u) {
+      e[u] = q0 + u < cnti ? S.nbr[(long long)(q0 + u) * n + i] : self;
+      SISPH_CHECK_ENTRY(S, e[u], self);
+    }
     float4 pj[8];
     float rjf[8];
     if constexpr (MX) {
@@ -436,6 +439,7 @@ __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
             const long long o = (long long)q * nwl + r;
             jj[u] = q < cnt ? S.widx[o] : w;
             ww[u] = q < cnt ? wc[o] : R(0);
+            SISPH_CHECK_IDX(S, jj[u], w);
           }
           R pv[8];
           _Pragma("unroll") for (int u = 0; u < 8; ++u) pv[u] = pc[jj[u]];

@@ -157,6 +157,7 @@ __device__ __forceinline__ void load_coef(const State &S, long long o, bool in, 
     j = in ? int(S.nbr[o] & kIdxMask) : i;
     cf = in ? static_cast<const double *>(S.coef)[o] : 0.0;
   }
+  SISPH_CHECK_IDX(S, j, i);
 }
 
 // ---------------------------------------------------------------------------
@@ -178,6 +179,7 @@ __device__ __forceinline__ R wall_pressure(const State &S, const R *pc, int r, i
       const long long o = (long long)q * nwl + r;
       jj[u] = q < cnt ? S.widx[o] : w;
       ww[u] = q < cnt ? wc[o] : R(0);
+      SISPH_CHECK_IDX(S, jj[u], w);
     }
     R pv[8];
     _Pragma("unroll") for (int u = 0; u < 8; ++u) pv[u] = pc[jj[u]];

@@ -28,6 +28,35 @@ constexpr int kErrCapacity = 1;   // a neighbour row overflowed its capacity
 constexpr int kErrTimeout = 2;    // a grid-barrier wait ran out of budget
 constexpr int kErrNonFinite = 4;  // a PPE residual was NaN / Inf
 constexpr int kErrNotConv = 8;    // a PPE solve stopped at max_iter
+constexpr int kErrInternal = 16;  // a checked build found a gathered index out of range
+
+// A build with SISPH_CHECKED defined bounds-checks every gathered neighbour
+// index before the access: an index outside [0, n) raises kErrInternal and
+// is replaced by the row's own index, so the access stays in bounds and the
+// host reports SISPH_EINTERNAL.  Without it the checks compile to nothing.
+#ifdef SISPH_CHECKED
+#define SISPH_CHECK_IDX(S, j, self)                        \
+  do {                                                      \
+    if (unsigned(j) >= unsigned((S).n)) {                   \
+      atomicOr((S).err, kErrInternal);                      \
+      (j) = (self);                                         \
+    }                                                       \
+  } while (0)
+#define SISPH_CHECK_ENTRY(S, e, self)                       \
+  do {                                                      \
+    if (((e) & kIdxMask) >= unsigned((S).n)) {              \
+      atomicOr((S).err, kErrInternal);                      \
+      (e) = (self);                                         \
+    }                                                       \
+  } while (0)
+#else
+#define SISPH_CHECK_IDX(S, j, self) \
+  do {                              \
+  } while (0)
+#define SISPH_CHECK_ENTRY(S, e, self) \
+  do {                                \
+  } while (0)
+#endif
 
 struct CaseDev {
   // cell grid
@@ -296,6 +325,7 @@ __device__ __forceinline__ R divr(R a, R b) {
       unsigned _e[8];                                                              \
       _Pragma("unroll") for (int _u = 0; _u < 8; ++_u) {                          \
         _e[_u] = _en[_u];                                                          \
+        SISPH_CHECK_ENTRY(S, _e[_u], _self);                                       \
         const int _q = _q0 + 8 + _u;                                               \
         _en[_u] = _q < _cnt ? S.nbr[(long long)_q * _n + i] : _self;              \
       }                                                                            \

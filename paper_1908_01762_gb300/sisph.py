@@ -14,6 +14,7 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libsisph.so")
+CHECKED_LIB_PATH = os.path.join(_PKG, "libsisph_checked.so")
 
 OK = 0
 EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, ENONFINITE, ETIMEOUT, EINTERNAL, ECAPACITY = (
@@ -69,11 +70,14 @@ class sisph_case_stats(C.Structure):
 _lib = None
 
 
-def load_library(path: str = LIB_PATH):
-    """Load libsisph.so (raises OSError if it is missing: no CPU fallback)."""
+def load_library(path: str = None):
+    """Load libsisph.so -- libsisph_checked.so when the environment sets
+    SISPH_CHECKED=1 -- (raises OSError if it is missing: no CPU fallback)."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = CHECKED_LIB_PATH if os.environ.get("SISPH_CHECKED") == "1" else LIB_PATH
     if not os.path.exists(path):
         raise OSError(f"libsisph.so not built ({path}); run paper_1908_01762_gb300.build()")
     L = C.CDLL(path)

@@ -34,6 +34,17 @@ def test_exports_every_declared_symbol(lib):
         assert hasattr(lib, n), n
 
 
+def test_checked_build_exports_every_declared_symbol():
+    # the variant that bounds-checks every gathered neighbour index on the
+    # device (SISPH_CHECKED) has the same C-ABI
+    from paper_1908_01762_gb300 import buildlib
+    path = buildlib.build(checked=True)
+    assert path.endswith("libsisph_checked.so")
+    checked = C.CDLL(path)
+    for n in _declared():
+        assert hasattr(checked, n), n
+
+
 def test_version_string(lib):
     from paper_1908_01762_gb300 import sisph
     assert "sm_103a" in sisph.sisph_version()
