@@ -190,7 +190,7 @@ void sisph_destroy(sisph_t s);
 
 /* Bring the neighbour lists to the current positions: N(i) = {j : |r_ij|^2 <
  * (3h)^2}, minimum image, exactly.  A case whose fluid moved more than s/2
- * since its last rebuild (every case, after sisph_set of a position) is first
+ * since its last rebuild (every case, after sisph_set moved a wall) is first
  * sorted into Morton-ordered cells and gets new skin lists; then every list is
  * filtered from its skin list.  sisph_step does this twice per step, leaving
  * out the pairs within a relative 4e-5 of the cutoff (|r_ij| > 3h(1 - 3e-5),
@@ -221,7 +221,9 @@ int sisph_ppe_solve(sisph_t s, double tol, int32_t max_iter, int32_t *iters, dou
  * max_iter in any of the steps (the state is still advanced and valid). */
 int sisph_step(sisph_t s, int32_t nsteps);
 
-/* Read or write a field (SISPH_F_*) for all particles in the caller's order. */
+/* Read or write a field (SISPH_F_*) for all particles in the caller's order.
+ * Writing a position needs no rebuild unless it moves a wall: the next
+ * refresh re-sorts the cases whose fluid moved more than s/2. */
 int sisph_get(sisph_t s, int32_t field, double *out);
 int sisph_set(sisph_t s, int32_t field, const double *in);
 

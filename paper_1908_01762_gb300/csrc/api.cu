@@ -1136,10 +1136,10 @@ int sisph_set(sisph_t s, int32_t field, const double *in) {
   if ((field == SISPH_F_Z || field == SISPH_F_W || field == SISPH_F_WT) && s->dim == 2)
     return fail(s, SISPH_EINVAL, "no third component in 2D");
   cudaError_t e = cudaMemcpyAsync(s->d_tmp, in, size_t(s->n) * sizeof(double), cudaMemcpyHostToDevice, s->stream);
-  if (e == cudaSuccess) e = launch_gather_field(S, L, s->d_tmp, dst);
+  // positions: fluid that moved past half the skin is re-sorted by the next
+  // refresh's own check; a wall that moved forces every case to be rebuilt
+  if (e == cudaSuccess) e = launch_gather_field(S, L, s->d_tmp, dst, field <= SISPH_F_Z);
   if (e == cudaSuccess) e = launch_refresh_mirrors(S, L);
-  // moved particles: the next refresh sorts and rebuilds every case
-  if (e == cudaSuccess && field <= SISPH_F_Z) e = force_rebuild(s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "set");
   return SISPH_OK;
@@ -1302,7 +1302,7 @@ static int copy_in(sisph_t s, const double *host, double *dst) {
   L.before = nullptr;
   L.after = nullptr;
   cudaError_t e = cudaMemcpyAsync(s->d_tmp, host, size_t(s->n) * sizeof(double), cudaMemcpyHostToDevice, s->stream);
-  if (e == cudaSuccess) e = launch_gather_field(s->S, L, s->d_tmp, dst);
+  if (e == cudaSuccess) e = launch_gather_field(s->S, L, s->d_tmp, dst, false);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   return e == cudaSuccess ? SISPH_OK : cuda_fail(s, e, "checkpoint write");
 }

@@ -572,10 +572,17 @@ __global__ void k_scatter_field(State S, const void *src, int is_float, int stri
   dst[S.uid[i]] = v;
 }
 
-__global__ void k_gather_field(State S, const double *src, double *dst) {
+// positions (moved_walls): a wall whose coordinate changes forces the next
+// refresh to rebuild every case (fluid moves are caught by the refresh's own
+// displacement check against the rebuild positions)
+__global__ void k_gather_field(State S, const double *src, double *dst, int moved_walls) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= S.n) return;
-  dst[i] = src[S.uid[i]];
+  const double v = src[S.uid[i]];
+  if (moved_walls && __double_as_longlong(v) != __double_as_longlong(dst[i]) &&
+      i >= S.cases[S.case_of[i]].wbeg)
+    *S.force = 1;
+  dst[i] = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -771,8 +778,9 @@ cudaError_t launch_scatter_disp(const State &S, const Launch &L, int comp, doubl
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather_field(const State &S, const Launch &L, const double *src_user, double *dst) {
-  k_gather_field<<<(S.n + 255) / 256, 256, 0, L.stream>>>(S, src_user, dst);
+cudaError_t launch_gather_field(const State &S, const Launch &L, const double *src_user, double *dst,
+                                bool positions) {
+  k_gather_field<<<(S.n + 255) / 256, 256, 0, L.stream>>>(S, src_user, dst, positions ? 1 : 0);
   return cudaGetLastError();
 }
 

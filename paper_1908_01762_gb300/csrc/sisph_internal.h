@@ -374,7 +374,8 @@ cudaError_t launch_speed_max(const State &S, const Launch &L, int which);
 cudaError_t launch_adapt_dt(const State &S, const Launch &L);
 cudaError_t launch_scatter_field(const State &S, const Launch &L, const void *src, int is_float,
                                  int stride_f4, int comp, double *dst_user);
-cudaError_t launch_gather_field(const State &S, const Launch &L, const double *src_user, double *dst);
+cudaError_t launch_gather_field(const State &S, const Launch &L, const double *src_user, double *dst,
+                                bool positions);
 cudaError_t launch_scatter_disp(const State &S, const Launch &L, int comp, double *dst_user);
 cudaError_t launch_refresh_mirrors(const State &S, const Launch &L);
 // ppe.cu
