@@ -315,7 +315,10 @@ def run_ours(args, rank, world):
     sisph.sisph_profile_enable(sim.h, False)
     t_ms = aggregate_time(t_ms, world, dev)
 
-    # algorithmic bytes (neighbour lists at the last r*)
+    # algorithmic bytes: the lists the step streamed (the last refresh, at
+    # r*, without the rim pairs); interactions: N(i) exactly
+    streamed = sim.get("ncount").astype(np.int64)
+    nskin = sim.get("nskin")
     counts, idx = sisph.sisph_neighbors(sim.h, n)
     starts = np.concatenate([[0], np.cumsum(counts)])
     fl = kinds == 0
@@ -330,7 +333,7 @@ def run_ours(args, rank, world):
         walls = np.nonzero(~flc)[0] + offs[ci]
         wall_counts = np.array([np.sum(fl[idx[starts[w]:starts[w + 1]]]) for w in walls]) \
             if walls.size else np.zeros(0)
-        fb, wb = sweep_bytes(cnt_c[flc], walls.size, wall_counts, rb)
+        fb, wb = sweep_bytes(streamed[sl][flc], walls.size, wall_counts, rb)
         its = float(it1[ci] - it0[ci])
         sweep_total += its * fb + (its + args.steps) * wb
         pairs += its * float(np.sum(cnt_c[flc]))
@@ -340,9 +343,8 @@ def run_ours(args, rank, world):
     if roof_site == "ppe_sweeps":
         per_launch_bytes = sweep_total / nk if nk else 0.0
     else:
-        nskin = sim.get("nskin")
-        per_launch_bytes = kernel_bytes(roof_site, mixed, dim, n_fluid, n, float(np.sum(counts[fl])),
-                                        float(np.sum(counts)), float(np.sum(nskin)))
+        per_launch_bytes = kernel_bytes(roof_site, mixed, dim, n_fluid, n, float(np.sum(streamed[fl])),
+                                        float(np.sum(streamed)), float(np.sum(nskin)))
     avg_ms = kern_ms / nk if nk else float("nan")
     traffic = measured_traffic(args.workload, roof_site, per_launch_bytes)
     achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9 if nk else None

@@ -165,7 +165,9 @@ typedef struct {
 #define SISPH_F_DY 18
 #define SISPH_F_DZ 19
 #define SISPH_F_NSKIN 20 /* length of the particle's skin list (read-only) */
-#define SISPH_F_COUNT 21
+#define SISPH_F_NCOUNT 21 /* length of its neighbour list as the last refresh left it
+                             (inside a step without the rim pairs; read-only) */
+#define SISPH_F_COUNT 22
 
 /* Fill defaults: FP64, omega 0.5, min_iter 2, eta 0.01, fs_ratio 0.8, ... */
 void sisph_default_options(sisph_options *opt);

@@ -695,7 +695,7 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
     A(&S.vf4, N); A(&S.utf4, N); A(&S.pf, N);
     A(&S.dgf[0], N); A(&S.dgf[1], N);
   }
-  A(&S.nbr, N * size_t(S.cap));
+  A(&S.nbr, ell_size(S.cap, (long long)N));
   A(&S.ncnt, N);
   A(&S.snbr, N * size_t(S.scap));
   A(&S.sncnt, N);
@@ -717,7 +717,7 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   // one 8-byte slot per ELL entry: packed index + FP32 coefficient, or FP64
   if (e == cudaSuccess) {
     char *q = nullptr;
-    e = dalloc(s, &q, N * size_t(S.cap) * 8);
+    e = dalloc(s, &q, ell_size(S.cap, (long long)N) * 8);
     S.coef = q;
   }
   AR(&S.prhs, N);
@@ -1107,10 +1107,11 @@ int sisph_get(sisph_t s, int32_t field, double *out) {
     case SISPH_F_DIAG: src = S.diag_out; break;
     case SISPH_F_DX: case SISPH_F_DY: case SISPH_F_DZ: break;
     case SISPH_F_NSKIN: src = S.sncnt; break;
+    case SISPH_F_NCOUNT: src = S.ncnt; break;
     default: return fail(s, SISPH_EINVAL, "unknown field");
   }
   if (field >= SISPH_F_DX && field <= SISPH_F_DZ) e = launch_scatter_disp(S, L, field - SISPH_F_DX, s->d_tmp);
-  else if (field == SISPH_F_NSKIN) e = launch_scatter_field(S, L, src, 2, 0, 0, s->d_tmp);
+  else if (field == SISPH_F_NSKIN || field == SISPH_F_NCOUNT) e = launch_scatter_field(S, L, src, 2, 0, 0, s->d_tmp);
   else e = launch_scatter_field(S, L, src, 0, 0, 0, s->d_tmp);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, s->d_tmp, size_t(s->n) * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -1149,7 +1150,7 @@ int sisph_neighbors(sisph_t s, int32_t *counts, int32_t *idx, int64_t idx_cap, i
   if (!valid_handle(s) || !counts) return fail(s, SISPH_EINVAL, "invalid handle or counts");
   const size_t N = size_t(s->n);
   std::vector<int> cnt(N), uid(N);
-  std::vector<unsigned> nbr(N * size_t(s->S.cap));
+  std::vector<unsigned> nbr(ell_size(s->S.cap, (long long)N));
   // the exact lists at the current positions (a step's own refreshes leave
   // out the pairs at the rim of the support)
   cudaError_t e = do_refresh(s, 0, false, true);
@@ -1177,7 +1178,7 @@ int sisph_neighbors(sisph_t s, int32_t *counts, int32_t *idx, int64_t idx_cap, i
   for (size_t u = 0; u < N; ++u) {
     int i = at[u];
     row.clear();
-    for (int k = 0; k < cnt[i]; ++k) row.push_back(uid[nbr[size_t(k) * N + i] & kIdxMask]);
+    for (int k = 0; k < cnt[i]; ++k) row.push_back(uid[nbr[ell_at(s->S.cap, k, i)] & kIdxMask]);
     std::sort(row.begin(), row.end());
     for (int v : row) idx[pos++] = v;
   }

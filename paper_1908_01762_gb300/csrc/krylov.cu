@@ -91,7 +91,7 @@ __device__ __forceinline__ R apply_row(const State &S, const CaseDev &P, int i, 
   const R al = R(alpha);
   const R yi = b ? a[i] - al * b[i] : a[i];
   if (!active) return yi;
-  const long long n = S.n;
+  const long long sb = slot_base(S, i);
   const int cnt = S.ncnt[i];
   const int fend = P.fbeg + P.nf;
   R acc = R(S.diag_out[i]) * yi;
@@ -100,7 +100,7 @@ __device__ __forceinline__ R apply_row(const State &S, const CaseDev &P, int i, 
     int jj[8];
     R cf[8];
     _Pragma("unroll") for (int u = 0; u < 8; ++u)
-      load_coef<R>(S, (long long)(q0 + u) * n + i, q0 + u < cnt, i, jj[u], cf[u]);
+      load_coef<R>(S, sb, q0 + u, q0 + u < cnt, i, jj[u], cf[u]);
     _Pragma("unroll") for (int u = 0; u < 8; ++u) {
       const int j = jj[u];
       R yj;

@@ -417,11 +417,10 @@ __global__ void __launch_bounds__(256) k_skin(State S) {
   const float cutf = float(P.cut2);
   const float lo_band = cutf * (1.0f - 1e-4f), hi_band = cutf * (1.0f + 1e-4f);
   const int zr = (DIM == 3) ? 1 : 0;
-  const long long nn = S.n;
   int cnt = 0;
   bool over = false;
   auto append = [&](unsigned entry) {
-    if (cnt < S.scap) S.snbr[(long long)cnt * nn + i] = entry;
+    if (cnt < S.scap) S.snbr[(long long)cnt * S.n + i] = entry;
     else over = true;
     ++cnt;
   };
@@ -594,15 +593,15 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
   // only fluid neighbour sits on the rim takes that neighbour's value
   const bool ex = EXACT || blockIdx.x >= unsigned(S.nft);
   const float lo_band = cut2f * (ex ? 1.0f - 1e-4f : 1.0f - 4e-5f), hi_band = cut2f * (1.0f + 1e-4f);
-  const long long nn = S.n;
   const int scnt = S.sncnt[i];
   const int head = S.wfin[i];
+  const long long sb = i;   // skin lists: entry q at q n + i
   int cnt = 0;
   bool over = false;
   unsigned band[kBand];
   int nband = 0;
   auto append = [&](unsigned entry) {
-    if (cnt < S.cap) S.nbr[(long long)cnt * nn + i] = entry;
+    if (cnt < S.cap) S.nbr[ell_at(S.cap, cnt, i)] = entry;
     else over = true;
     ++cnt;
   };
@@ -615,7 +614,7 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
   for (int q0 = 0; q0 < head; q0 += 4) {
     unsigned h4[4];
     _Pragma("unroll") for (int u = 0; u < 4; ++u)
-      h4[u] = q0 + u < head ? S.snbr[(long long)(q0 + u) * nn + i] : 0u;
+      h4[u] = q0 + u < head ? S.snbr[sb + (long long)(q0 + u) * S.n] : 0u;
     _Pragma("unroll") for (int u = 0; u < 4; ++u) {
       SISPH_CHECK_ENTRY(S, h4[u], unsigned(i));
       if (q0 + u < head) append(h4[u]);
@@ -625,7 +624,8 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
   // gathered (a slot past the row's end reads the row itself)
   const unsigned self = unsigned(i) | (stencil_code(0, 0, 0) << kCodeShift);
   unsigned en[kU];
-  _Pragma("unroll") for (int u = 0; u < kU; ++u) en[u] = head + u < scnt ? S.snbr[(long long)(head + u) * nn + i] : self;
+  _Pragma("unroll") for (int u = 0; u < kU; ++u)
+    en[u] = head + u < scnt ? S.snbr[sb + (long long)(head + u) * S.n] : self;
   for (int q0 = head; q0 < scnt; q0 += kU) {
     unsigned e[kU];
     float4 pj[kU];
@@ -636,7 +636,7 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
     }
     _Pragma("unroll") for (int u = 0; u < kU; ++u) {
       const int q = q0 + kU + u;
-      en[u] = q < scnt ? S.snbr[(long long)q * nn + i] : self;
+      en[u] = q < scnt ? S.snbr[sb + (long long)q * S.n] : self;
     }
     _Pragma("unroll") for (int u = 0; u < kU; ++u) {
       if (q0 + u >= scnt) continue;

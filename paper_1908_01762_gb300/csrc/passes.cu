@@ -70,10 +70,10 @@ __device__ __forceinline__ void tvel(const State &S, int j, R u[3]) {
 #define ROW_LOOP_FROM(S, i, k0, ...)                          \
   {                                                            \
     const int _cnt = S.ncnt[i];                                \
-    const long long _n = S.n;                                  \
+    const long long _b = ell_base(S.cap, i);                   \
     _Pragma("unroll 4")                                        \
     for (int _k = (k0); _k < _cnt; ++_k) {                     \
-      unsigned e = S.nbr[(long long)_k * _n + i];              \
+      unsigned e = S.nbr[_b + (long long)_k * 256];            \
       SISPH_CHECK_ENTRY(S, e, unsigned(i));                    \
       __VA_ARGS__                                              \
     }                                                          \

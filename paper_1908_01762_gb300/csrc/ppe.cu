@@ -142,7 +142,7 @@ __global__ void k_setup_fluid(State S) {
         }
       }
       if (valid) {
-        store_coef<R>(S.coef, (long long)k * _n + i, j, fac);
+        store_coef<R>(S.coef, slot_at(S, k, i), j, fac);
         if (S.p2p && j != i) {
           const int dt = S.tile_of[j];
           if (dt != int(blockIdx.x)) deps.insert(dt);
@@ -202,7 +202,7 @@ __device__ __forceinline__ void wall_row(const State &S, const Tile &t, int i, D
   R sw = R(0), acc[3] = {R(0), R(0), R(0)};
   int cnt = 0;
   const int cnti = S.ncnt[i];
-  const long long n = S.n, nw = S.nw;
+  const long long nw = S.nw;
   R *wc = static_cast<R *>(S.wcoef);
   // fluid neighbours only: they follow the row's wall head.  Chunks of 8:
   // the entries, then the gathers, go out together before any store.
@@ -210,7 +210,7 @@ __device__ __forceinline__ void wall_row(const State &S, const Tile &t, int i, D
   for (int q0 = S.wfin[i]; q0 < cnti; q0 += 8) {
     unsigned e[8];
     _Pragma("unroll") for (int u = 0; u < 8; ++u) {
-      e[u] = q0 + u < cnti ? S.nbr[(long long)(q0 + u) * n + i] : self;
+      e[u] = q0 + u < cnti ? S.nbr[ell_at(S.cap, q0 + u, i)] : self;
       SISPH_CHECK_ENTRY(S, e[u], self);
     }
     float4 pj[8];
@@ -271,12 +271,12 @@ __global__ void k_setup_wall(State S) {
 // coefficient.
 template <typename R>
 __device__ __forceinline__ R jacobi_sum(const State &S, const R *pc, int i, R acc, int cnt) {
-  const long long n = S.n;
+  const long long sb = slot_base(S, i);
   for (int q0 = 0; q0 < cnt; q0 += 8) {
     int jj[8];
     R cf[8];
     _Pragma("unroll") for (int u = 0; u < 8; ++u)
-      load_coef<R>(S, (long long)(q0 + u) * n + i, q0 + u < cnt, i, jj[u], cf[u]);
+      load_coef<R>(S, sb, q0 + u, q0 + u < cnt, i, jj[u], cf[u]);
     R pj[8];
     _Pragma("unroll") for (int u = 0; u < 8; ++u) pj[u] = pc[jj[u]];
     _Pragma("unroll") for (int u = 0; u < 8; ++u) acc += cf[u] * pj[u];
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
   const R *wc = static_cast<const R *>(S.wcoef);
   const R *wsinv = static_cast<const R *>(S.wsinv);
   const R *wh = static_cast<const R *>(S.wh);
-  const long long n = S.n, nwl = S.nw;
+  const long long nwl = S.nw;
   int *done = S.act;                 // [nc] case finished
   int *fin = S.act + nc;             // [nc] sweep count at which it finished
   unsigned *arrive = reinterpret_cast<unsigned *>(S.par + nc);  // [nc]
@@ -486,11 +486,12 @@ __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
       if (i < t.end) {
         R acc = prhs[i];
         const int cnt = S.ncnt[i];
+        const long long sb = slot_base(S, i);
         for (int q0 = 0; q0 < cnt; q0 += 8) {
           int jj[8];
           R cf[8];
           _Pragma("unroll") for (int u = 0; u < 8; ++u)
-            load_coef<R>(S, (long long)(q0 + u) * n + i, q0 + u < cnt, i, jj[u], cf[u]);
+            load_coef<R>(S, sb, q0 + u, q0 + u < cnt, i, jj[u], cf[u]);
           R pj[8];
           _Pragma("unroll") for (int u = 0; u < 8; ++u) pj[u] = pc[jj[u]];
           _Pragma("unroll") for (int u = 0; u < 8; ++u) acc += cf[u] * pj[u];

@@ -145,10 +145,21 @@ __device__ __forceinline__ void store_coef(void *base, long long o, int j, R fac
     static_cast<double *>(base)[o] = fac;
 }
 
-// Slot o of row i: neighbour j and coefficient (a slot past the row's end,
-// in[u] false, reads the row itself with a zero coefficient).
+// The slots are stored in blocks of 256 consecutive particles: slot q of
+// particle i at ((i / 256) cap + q) 256 + i % 256.  A warp's 32 rows read one
+// contiguous run per slot row, and the slot rows of a block follow each other
+// (2-kB runs of 8-byte slots), so a sweep streams whole DRAM pages instead of
+// one 256-byte piece per page.
+__device__ __forceinline__ long long slot_base(const State &S, int i) { return ell_base(S.cap, i); }
+__device__ __forceinline__ long long slot_at(const State &S, int q, int i) { return ell_at(S.cap, q, i); }
+
+// Slot q of row i (base = slot_base(S, i)): neighbour j and coefficient (a
+// slot past the row's end, in false, reads the row itself with a zero
+// coefficient).
 template <typename R>
-__device__ __forceinline__ void load_coef(const State &S, long long o, bool in, int i, int &j, R &cf) {
+__device__ __forceinline__ void load_coef(const State &S, long long base, int q, bool in, int i, int &j,
+                                          R &cf) {
+  const long long o = base + (long long)q * 256;
   if constexpr (std::is_same<R, float>::value) {
     const uint2 v = in ? static_cast<const uint2 *>(S.coef)[o] : make_uint2(unsigned(i), 0u);
     j = int(v.x);

@@ -20,6 +20,21 @@ namespace sisph {
 constexpr int kCodeShift = 26;                   // neighbour entry = j | code << 26
 constexpr unsigned kIdxMask = (1u << kCodeShift) - 1u;
 constexpr int kMaxParticles = (1 << kCodeShift) - 1;
+
+// Neighbour lists and PPE slots are stored in blocks of 256 consecutive
+// particles: entry q of particle i at ((i / 256) cap + q) 256 + i % 256.  A
+// warp's 32 rows read one contiguous run per entry, and the entries of a
+// block follow each other (1-2 kB runs), so the streams fill whole DRAM
+// pages instead of one 128-256-byte piece per page.  (Skin lists, read once
+// per refresh by the filter, keep entry q at q n + i.)
+__host__ __device__ __forceinline__ long long ell_base(int cap, long long i) {
+  return (i >> 8) * cap * 256 + (i & 255);
+}
+__host__ __device__ __forceinline__ long long ell_at(int cap, int q, long long i) {
+  return ell_base(cap, i) + (long long)q * 256;
+}
+// elements of a blocked list array of n particles
+inline size_t ell_size(int cap, long long n) { return size_t((n + 255) / 256) * 256 * size_t(cap); }
 constexpr int kMaxCellsPerAxis = (1 << 21) - 1;     // packed rebuild cell: 21 bits per axis
 constexpr int kDepCap = 96;                         // dependency list of a tile
 
@@ -316,18 +331,18 @@ __device__ __forceinline__ R divr(R a, R b) {
 #define ROW_CHUNKS(S, i, ...)                                                      \
   {                                                                                \
     const int _cnt = S.ncnt[i];                                                    \
-    const long long _n = S.n;                                                      \
+    const long long _b = ell_base(S.cap, i);                                       \
     const unsigned _self = unsigned(i) | (stencil_code(0, 0, 0) << kCodeShift);    \
     unsigned _en[8];                                                               \
     _Pragma("unroll") for (int _u = 0; _u < 8; ++_u)                              \
-      _en[_u] = _u < _cnt ? S.nbr[(long long)_u * _n + i] : _self;                \
+      _en[_u] = _u < _cnt ? S.nbr[_b + (long long)_u * 256] : _self;              \
     for (int _q0 = 0; _q0 < _cnt; _q0 += 8) {                                      \
       unsigned _e[8];                                                              \
       _Pragma("unroll") for (int _u = 0; _u < 8; ++_u) {                          \
         _e[_u] = _en[_u];                                                          \
         SISPH_CHECK_ENTRY(S, _e[_u], _self);                                       \
         const int _q = _q0 + 8 + _u;                                               \
-        _en[_u] = _q < _cnt ? S.nbr[(long long)_q * _n + i] : _self;              \
+        _en[_u] = _q < _cnt ? S.nbr[_b + (long long)_q * 256] : _self;            \
       }                                                                            \
       _Pragma("unroll") for (int _u = 0; _u < 8; ++_u) {                          \
         const unsigned e = _e[_u];                                                 \

@@ -24,7 +24,7 @@ FP64, MIXED = 0, 1
 PREF_FIXED, PREF_TWICE_MAX_FIRST, PREF_EXTERNAL = 0, 1, 2
 FIELDS = {"x": 0, "y": 1, "z": 2, "u": 3, "v": 4, "w": 5, "ut": 6, "vt": 7, "wt": 8, "p": 9,
           "rho": 10, "m": 11, "nx": 12, "ny": 13, "nz": 14, "rhs": 15, "diag": 16,
-          "dx": 17, "dy": 18, "dz": 19, "nskin": 20}
+          "dx": 17, "dy": 18, "dz": 19, "nskin": 20, "ncount": 21}
 _NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA",
           ENOTCONVERGED: "ENOTCONVERGED", ENONFINITE: "ENONFINITE", ETIMEOUT: "ETIMEOUT",
           EINTERNAL: "EINTERNAL", ECAPACITY: "ECAPACITY"}
