@@ -75,14 +75,25 @@ SITES = {"check": "nbr.cu", "sort": "nbr.cu", "build": "nbr.cu", "sync": "nbr.cu
          "update": "passes.cu", "speed_max": "passes.cu", "adapt_dt": "passes.cu"}
 
 
+def kernel_source_sha(site):
+    """sha1 (12 hex digits) of the source a site's kernel is built from: its
+    translation unit and the shared device headers."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1908_01762_gb300", "csrc")
+    h = hashlib.sha1()
+    for name in (SITES[site], "sisph_internal.h", "ppe_sync.cuh"):
+        h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:12]
+
+
 def measured_traffic(workload, site, per_launch_bytes):
     """DRAM bytes (read + write) per launch of one kernel, from the committed
     ncu summary profiles/<site>_<workload>_traffic.md: the DRAM bytes of the
     captured launch per algorithmic byte of that launch, times this run's
     algorithmic bytes per launch (a captured solve may take more or fewer
     sweeps than the average one).  None if there is no summary or the
-    kernel's source file changed since the counters were taken."""
-    import hashlib
+    kernel's source (its file or the shared device headers) changed since the
+    counters were taken."""
     path = os.path.join(ROOT, "profiles", f"{site}_{workload}_traffic.md")
     if not os.path.exists(path) or not per_launch_bytes:
         return None
@@ -92,9 +103,8 @@ def measured_traffic(workload, site, per_launch_bytes):
                                                           "kernel_source_sha1"):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    src = os.path.join(ROOT, "paper_1908_01762_gb300", "csrc", SITES[site])
-    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
-    if vals.get("kernel_source_sha1") != sha or "dram_bytes_per_algorithmic_byte" not in vals:
+    if vals.get("kernel_source_sha1") != kernel_source_sha(site) or \
+            "dram_bytes_per_algorithmic_byte" not in vals:
         return None
     return float(vals["dram_bytes_per_algorithmic_byte"]) * per_launch_bytes
 

@@ -1,7 +1,6 @@
 """Host-side pieces of bench.py: the algorithmic byte models of the roofline
 and the reading of the committed ncu traffic summaries (no GPU needed)."""
 import glob
-import hashlib
 import os
 
 import numpy as np
@@ -43,8 +42,7 @@ def test_traffic_summaries_are_read_only_for_the_kernel_they_measured(path):
             vals[k.strip()] = v.strip()
     ratio = float(vals["dram_bytes_per_algorithmic_byte"])
     assert ratio > 0
-    src = os.path.join(ROOT, "paper_1908_01762_gb300", "csrc", bench.SITES[site])
-    current = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    current = bench.kernel_source_sha(site)
     got = bench.measured_traffic(workload, site, 1.0e9)
     if vals["kernel_source_sha1"] == current:
         assert got == pytest.approx(ratio * 1.0e9)
