@@ -73,7 +73,7 @@ __device__ __forceinline__ void tvel(const State &S, int j, R u[3]) {
     const long long _b = ell_base(S.cap, i);                   \
     _Pragma("unroll 4")                                        \
     for (int _k = (k0); _k < _cnt; ++_k) {                     \
-      unsigned e = S.nbr[_b + (long long)_k * 256];            \
+      unsigned e = S.nbr[_b + (long long)_k * kEllBlock];      \
       SISPH_CHECK_ENTRY(S, e, unsigned(i));                    \
       __VA_ARGS__                                              \
     }                                                          \

@@ -145,11 +145,8 @@ __device__ __forceinline__ void store_coef(void *base, long long o, int j, R fac
     static_cast<double *>(base)[o] = fac;
 }
 
-// The slots are stored in blocks of 256 consecutive particles: slot q of
-// particle i at ((i / 256) cap + q) 256 + i % 256.  A warp's 32 rows read one
-// contiguous run per slot row, and the slot rows of a block follow each other
-// (2-kB runs of 8-byte slots), so a sweep streams whole DRAM pages instead of
-// one 256-byte piece per page.
+// The slots share the neighbour lists' blocked layout (ell_at): a warp's rows
+// stream one contiguous run of 256-byte slot rows.
 __device__ __forceinline__ long long slot_base(const State &S, int i) { return ell_base(S.cap, i); }
 __device__ __forceinline__ long long slot_at(const State &S, int q, int i) { return ell_at(S.cap, q, i); }
 
@@ -159,7 +156,7 @@ __device__ __forceinline__ long long slot_at(const State &S, int q, int i) { ret
 template <typename R>
 __device__ __forceinline__ void load_coef(const State &S, long long base, int q, bool in, int i, int &j,
                                           R &cf) {
-  const long long o = base + (long long)q * 256;
+  const long long o = base + (long long)q * kEllBlock;
   if constexpr (std::is_same<R, float>::value) {
     const uint2 v = in ? static_cast<const uint2 *>(S.coef)[o] : make_uint2(unsigned(i), 0u);
     j = int(v.x);

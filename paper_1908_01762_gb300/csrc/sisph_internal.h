@@ -21,20 +21,23 @@ constexpr int kCodeShift = 26;                   // neighbour entry = j | code <
 constexpr unsigned kIdxMask = (1u << kCodeShift) - 1u;
 constexpr int kMaxParticles = (1 << kCodeShift) - 1;
 
-// Neighbour lists and PPE slots are stored in blocks of 256 consecutive
-// particles: entry q of particle i at ((i / 256) cap + q) 256 + i % 256.  A
-// warp's 32 rows read one contiguous run per entry, and the entries of a
-// block follow each other (1-2 kB runs), so the streams fill whole DRAM
-// pages instead of one 128-256-byte piece per page.  (Skin lists, read once
-// per refresh by the filter, keep entry q at q n + i.)
+// Neighbour lists and PPE slots are stored in blocks of 32 consecutive
+// particles, one warp's rows: entry q of particle i at ((i / 32) cap + q) 32
+// + i % 32.  The entries of a warp's rows follow each other, so a warp
+// streams one contiguous run (cap entries of 128 or 256 bytes) and fills
+// whole DRAM pages instead of one piece per page.  (Skin lists, read once per
+// refresh by the filter, keep entry q at q n + i.)
+constexpr int kEllBlock = 32;    // particles per block (a power of two)
 __host__ __device__ __forceinline__ long long ell_base(int cap, long long i) {
-  return (i >> 8) * cap * 256 + (i & 255);
+  return (i / kEllBlock) * cap * kEllBlock + (i % kEllBlock);
 }
 __host__ __device__ __forceinline__ long long ell_at(int cap, int q, long long i) {
-  return ell_base(cap, i) + (long long)q * 256;
+  return ell_base(cap, i) + (long long)q * kEllBlock;
 }
 // elements of a blocked list array of n particles
-inline size_t ell_size(int cap, long long n) { return size_t((n + 255) / 256) * 256 * size_t(cap); }
+inline size_t ell_size(int cap, long long n) {
+  return size_t((n + kEllBlock - 1) / kEllBlock) * kEllBlock * size_t(cap);
+}
 constexpr int kMaxCellsPerAxis = (1 << 21) - 1;     // packed rebuild cell: 21 bits per axis
 constexpr int kDepCap = 96;                         // dependency list of a tile
 
@@ -335,14 +338,14 @@ __device__ __forceinline__ R divr(R a, R b) {
     const unsigned _self = unsigned(i) | (stencil_code(0, 0, 0) << kCodeShift);    \
     unsigned _en[8];                                                               \
     _Pragma("unroll") for (int _u = 0; _u < 8; ++_u)                              \
-      _en[_u] = _u < _cnt ? S.nbr[_b + (long long)_u * 256] : _self;              \
+      _en[_u] = _u < _cnt ? S.nbr[_b + (long long)_u * kEllBlock] : _self;        \
     for (int _q0 = 0; _q0 < _cnt; _q0 += 8) {                                      \
       unsigned _e[8];                                                              \
       _Pragma("unroll") for (int _u = 0; _u < 8; ++_u) {                          \
         _e[_u] = _en[_u];                                                          \
         SISPH_CHECK_ENTRY(S, _e[_u], _self);                                       \
         const int _q = _q0 + 8 + _u;                                               \
-        _en[_u] = _q < _cnt ? S.nbr[_b + (long long)_q * 256] : _self;            \
+        _en[_u] = _q < _cnt ? S.nbr[_b + (long long)_q * kEllBlock] : _self;      \
       }                                                                            \
       _Pragma("unroll") for (int _u = 0; _u < 8; ++_u) {                          \
         const unsigned e = _e[_u];                                                 \
