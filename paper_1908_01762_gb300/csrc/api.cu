@@ -697,7 +697,7 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   }
   A(&S.nbr, ell_size(S.cap, (long long)N));
   A(&S.ncnt, N);
-  A(&S.snbr, N * size_t(S.scap));
+  A(&S.snbr, ell_size(S.scap, (long long)N));
   A(&S.sncnt, N);
   A(&S.wfin, N);
   A(&S.cell, N);

@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(256) k_skin(State S) {
   int cnt = 0;
   bool over = false;
   auto append = [&](unsigned entry) {
-    if (cnt < S.scap) S.snbr[(long long)cnt * S.n + i] = entry;
+    if (cnt < S.scap) S.snbr[ell_at(S.scap, cnt, i)] = entry;
     else over = true;
     ++cnt;
   };
@@ -595,7 +595,7 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
   const float lo_band = cut2f * (ex ? 1.0f - 1e-4f : 1.0f - 4e-5f), hi_band = cut2f * (1.0f + 1e-4f);
   const int scnt = S.sncnt[i];
   const int head = S.wfin[i];
-  const long long sb = i;   // skin lists: entry q at q n + i
+  const long long sb = ell_base(S.scap, i);
   int cnt = 0;
   bool over = false;
   unsigned band[kBand];
@@ -614,7 +614,7 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
   for (int q0 = 0; q0 < head; q0 += 4) {
     unsigned h4[4];
     _Pragma("unroll") for (int u = 0; u < 4; ++u)
-      h4[u] = q0 + u < head ? S.snbr[sb + (long long)(q0 + u) * S.n] : 0u;
+      h4[u] = q0 + u < head ? S.snbr[sb + (long long)(q0 + u) * kEllBlock] : 0u;
     _Pragma("unroll") for (int u = 0; u < 4; ++u) {
       SISPH_CHECK_ENTRY(S, h4[u], unsigned(i));
       if (q0 + u < head) append(h4[u]);
@@ -625,7 +625,7 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
   const unsigned self = unsigned(i) | (stencil_code(0, 0, 0) << kCodeShift);
   unsigned en[kU];
   _Pragma("unroll") for (int u = 0; u < kU; ++u)
-    en[u] = head + u < scnt ? S.snbr[sb + (long long)(head + u) * S.n] : self;
+    en[u] = head + u < scnt ? S.snbr[sb + (long long)(head + u) * kEllBlock] : self;
   for (int q0 = head; q0 < scnt; q0 += kU) {
     unsigned e[kU];
     float4 pj[kU];
@@ -636,7 +636,7 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
     }
     _Pragma("unroll") for (int u = 0; u < kU; ++u) {
       const int q = q0 + kU + u;
-      en[u] = q < scnt ? S.snbr[sb + (long long)q * S.n] : self;
+      en[u] = q < scnt ? S.snbr[sb + (long long)q * kEllBlock] : self;
     }
     _Pragma("unroll") for (int u = 0; u < kU; ++u) {
       if (q0 + u >= scnt) continue;

@@ -21,12 +21,11 @@ constexpr int kCodeShift = 26;                   // neighbour entry = j | code <
 constexpr unsigned kIdxMask = (1u << kCodeShift) - 1u;
 constexpr int kMaxParticles = (1 << kCodeShift) - 1;
 
-// Neighbour lists and PPE slots are stored in blocks of 32 consecutive
-// particles, one warp's rows: entry q of particle i at ((i / 32) cap + q) 32
-// + i % 32.  The entries of a warp's rows follow each other, so a warp
-// streams one contiguous run (cap entries of 128 or 256 bytes) and fills
-// whole DRAM pages instead of one piece per page.  (Skin lists, read once per
-// refresh by the filter, keep entry q at q n + i.)
+// Neighbour lists, skin lists and PPE slots are stored in blocks of 32
+// consecutive particles, one warp's rows: entry q of particle i at
+// ((i / 32) cap + q) 32 + i % 32.  The entries of a warp's rows follow each
+// other, so a warp streams one contiguous run (cap entries of 128 or 256
+// bytes) and fills whole DRAM pages instead of one piece per page.
 constexpr int kEllBlock = 32;    // particles per block (a power of two)
 __host__ __device__ __forceinline__ long long ell_base(int cap, long long i) {
   return (i / kEllBlock) * cap * kEllBlock + (i % kEllBlock);
