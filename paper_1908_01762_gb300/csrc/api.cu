@@ -727,8 +727,8 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
   A(&S.diag_out, N);
   size_t NW = std::max<size_t>(1, size_t(s->nw));
   A(&S.wcnt, NW);
-  A(&S.widx, NW * size_t(S.wcap));
-  AR(&S.wcoef, NW * size_t(S.wcap));
+  A(&S.widx, ell_size(S.wcap, (long long)NW));
+  AR(&S.wcoef, ell_size(S.wcap, (long long)NW));
   AR(&S.wsinv, NW);
   AR(&S.wh, NW);
   A(&S.tile_part, 8 * size_t(std::max(1, S.nft)));   // four sweeps in flight

@@ -59,7 +59,6 @@ __device__ __forceinline__ Vecs<R> vecs(const State &S) {
 template <typename R>
 __device__ __forceinline__ R wall_linear(const State &S, const R *a, const R *b, double alpha, int r, int w) {
   const R *wc = static_cast<const R *>(S.wcoef);
-  const long long nwl = S.nw;
   const int cnt = S.wcnt[r];
   const R al = R(alpha);
   R acc = R(0);
@@ -68,7 +67,7 @@ __device__ __forceinline__ R wall_linear(const State &S, const R *a, const R *b,
     R ww[8];
     _Pragma("unroll") for (int u = 0; u < 8; ++u) {
       const int q = q0 + u;
-      const long long o = (long long)q * nwl + r;
+      const long long o = ell_at(S.wcap, q, r);
       jj[u] = q < cnt ? S.widx[o] : w;
       ww[u] = q < cnt ? wc[o] : R(0);
       SISPH_CHECK_IDX(S, jj[u], w);

@@ -83,7 +83,7 @@ __device__ __forceinline__ void tvel(const State &S, int j, R u[3]) {
 // Summation density, Eq. summation_density, for fluid particles.
 // ---------------------------------------------------------------------------
 template <int DIM, bool MX>
-__global__ void k_density(State S) {
+__global__ void __launch_bounds__(256, MX ? 6 : 3) k_density(State S) {
   using R = typename Geo<DIM, MX>::R;
   const Tile &t = S.ftiles[blockIdx.x];
   int i = t.beg + threadIdx.x;
@@ -452,7 +452,7 @@ __global__ void k_gtvf(State S, int sub, int cur, int skip_k1) {
 // takes the pressure gradient here; its GTVF and update run as separate passes.
 // ---------------------------------------------------------------------------
 template <int DIM>
-__global__ void k_pgrad_gtvf1(State S) {
+__global__ void __launch_bounds__(256, 5) k_pgrad_gtvf1(State S) {
   const Tile &t = S.ftiles[blockIdx.x];
   int i = t.beg + threadIdx.x;
   if (i >= t.end) return;

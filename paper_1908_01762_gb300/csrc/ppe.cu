@@ -202,7 +202,6 @@ __device__ __forceinline__ void wall_row(const State &S, const Tile &t, int i, D
   R sw = R(0), acc[3] = {R(0), R(0), R(0)};
   int cnt = 0;
   const int cnti = S.ncnt[i];
-  const long long nw = S.nw;
   R *wc = static_cast<R *>(S.wcoef);
   // fluid neighbours only: they follow the row's wall head.  Chunks of 8:
   // the entries, then the gathers, go out together before any store.
@@ -238,8 +237,8 @@ __device__ __forceinline__ void wall_row(const State &S, const Tile &t, int i, D
       }
       R w = K.sig * poly_w<R>(qof<R>(sqrt_r(r2), K.h, K.ih));
       if (S.p2p) deps.insert(S.tile_of[j]);
-      S.widx[(long long)cnt * nw + r] = j;
-      wc[(long long)cnt * nw + r] = w;
+      S.widx[ell_at(S.wcap, cnt, r)] = j;
+      wc[ell_at(S.wcap, cnt, r)] = w;
       ++cnt;
       sw += w;
       _Pragma("unroll") for (int q = 0; q < DIM; ++q) acc[q] += rj * d[q] * w;
@@ -398,7 +397,6 @@ __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
   const R *wc = static_cast<const R *>(S.wcoef);
   const R *wsinv = static_cast<const R *>(S.wsinv);
   const R *wh = static_cast<const R *>(S.wh);
-  const long long nwl = S.nw;
   int *done = S.act;                 // [nc] case finished
   int *fin = S.act + nc;             // [nc] sweep count at which it finished
   unsigned *arrive = reinterpret_cast<unsigned *>(S.par + nc);  // [nc]
@@ -436,7 +434,7 @@ __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
           R ww[8];
           _Pragma("unroll") for (int u = 0; u < 8; ++u) {
             const int q = q0 + u;
-            const long long o = (long long)q * nwl + r;
+            const long long o = ell_at(S.wcap, q, r);
             jj[u] = q < cnt ? S.widx[o] : w;
             ww[u] = q < cnt ? wc[o] : R(0);
             SISPH_CHECK_IDX(S, jj[u], w);

@@ -176,7 +176,6 @@ __device__ __forceinline__ void load_coef(const State &S, long long base, int q,
 template <typename R>
 __device__ __forceinline__ R wall_pressure(const State &S, const R *pc, int r, int w, int c) {
   const R *wc = static_cast<const R *>(S.wcoef);
-  const long long nwl = S.nw;
   R acc = static_cast<const R *>(S.wh)[r];
   const int cnt = S.wcnt[r];
   for (int q0 = 0; q0 < cnt; q0 += 8) {
@@ -184,7 +183,7 @@ __device__ __forceinline__ R wall_pressure(const State &S, const R *pc, int r, i
     R ww[8];
     _Pragma("unroll") for (int u = 0; u < 8; ++u) {
       const int q = q0 + u;
-      const long long o = (long long)q * nwl + r;
+      const long long o = ell_at(S.wcap, q, r);
       jj[u] = q < cnt ? S.widx[o] : w;
       ww[u] = q < cnt ? wc[o] : R(0);
       SISPH_CHECK_IDX(S, jj[u], w);
