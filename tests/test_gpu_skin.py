@@ -139,3 +139,55 @@ def test_checkpoint_with_a_pending_rebuild(sisph, tmp_path):
         assert np.array_equal(a.get(f), b.get(f)), f
     a.close()
     b.close()
+
+
+def test_setting_positions_rebuilds_only_what_moved(sisph):
+    case = workloads.dam_break_2d(dx=0.04)
+    sim = sisph.Simulation(case, precision=sisph.MIXED)
+    sim.step(2)
+    sim.build_neighbors()
+    before = sim.stats()[0].rebuilds
+    # the same positions written back: nothing moved, no rebuild
+    for f in ("x", "y"):
+        sim.set(f, sim.get(f))
+    sim.build_neighbors()
+    assert sim.stats()[0].rebuilds == before
+    # a wall moved (by a tenth of its spacing): every case is re-sorted
+    x = sim.get("x")
+    w = np.nonzero(case["kind"] == 1)[0][0]
+    x[w] += 0.004
+    sim.set("x", x)
+    sim.build_neighbors()
+    assert sim.stats()[0].rebuilds == before + 1
+    assert_lists_exact(sim, case)
+    sim.close()
+
+
+@pytest.mark.parametrize("name", ["db2d", "db3d"])
+def test_step_lists_leave_out_only_the_rim(sisph, name):
+    # inside a step the fluid rows drop the pairs within a relative 4e-5 of
+    # the cutoff; the API's lists are exact: every dropped pair lies there
+    case = {"db2d": lambda: workloads.dam_break_2d(dx=0.04),
+            "db3d": lambda: workloads.dam_break_3d(dx=0.05)}[name]()
+    # a time step so small that the step's last refresh (at r*) and the
+    # current positions agree far inside the 2e-5 margin of the rim
+    case["params"] = dict(case["params"], dt=1e-10)
+    sim = sisph.Simulation(case, precision=sisph.MIXED)
+    sim.step(3)
+    streamed = sim.get("ncount").astype(np.int64)      # the step's last refresh
+    counts, idx = sim.neighbors()                       # exact, at the current positions
+    fluid = case["kind"] == 0
+    assert np.all(streamed[~fluid] == counts[~fluid])   # wall rows stay exact
+    assert np.all(streamed[fluid] <= counts[fluid])
+    # the pairs that were left out sit within 3h (1 - 3e-5) .. 3h
+    dim = case["dim"]
+    pos = np.stack([sim.get(c) for c in ("x", "y", "z")[:dim]], 1)
+    h = case["params"]["h"]
+    starts = np.concatenate([[0], np.cumsum(counts)])
+    rows = np.nonzero(fluid & (streamed < counts))[0]
+    for i in rows[:200]:
+        js = idx[starts[i]:starts[i + 1]]
+        r = np.sqrt(np.sum((pos[js] - pos[i]) ** 2, axis=1))
+        near_rim = np.sum(r > 3 * h * (1 - 3e-5))
+        assert counts[i] - streamed[i] <= near_rim, i
+    sim.close()
