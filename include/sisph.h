@@ -223,6 +223,11 @@ int sisph_ppe_solve(sisph_t s, double tol, int32_t max_iter, int32_t *iters, dou
  * max_iter in any of the steps (the state is still advanced and valid). */
 int sisph_step(sisph_t s, int32_t nsteps);
 
+/* sisph_step on a batch handle (Algorithm 1 for every case at once), with
+ * iters_per_case[c] (ncases entries; may be NULL) set to the PPE sweeps case c
+ * took over these nsteps steps.  Same return codes as sisph_step. */
+int sisph_batch_step(sisph_t s, int32_t nsteps, int32_t *iters_per_case);
+
 /* Read or write a field (SISPH_F_*) for all particles in the caller's order.
  * Writing a position needs no rebuild unless it moves a wall: the next
  * refresh re-sorts the cases whose fluid moved more than s/2. */

@@ -1185,6 +1185,27 @@ int sisph_neighbors(sisph_t s, int32_t *counts, int32_t *idx, int64_t idx_cap, i
   return SISPH_OK;
 }
 
+int sisph_batch_step(sisph_t s, int32_t nsteps, int32_t *iters_per_case) {
+  NvtxScope nvtx("sisph_batch_step");
+  if (!valid_handle(s)) return fail(s, SISPH_EINVAL, "invalid handle");
+  const int nc = s->ncases;
+  std::vector<long long> t0(nc), t1(nc);
+  if (iters_per_case) {
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(t0.data(), s->S.iters_tot, nc * sizeof(long long), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(s, e, "batch_step");
+  }
+  const int rc = sisph_step(s, nsteps);
+  if (rc != SISPH_OK && rc != SISPH_ENOTCONVERGED) return rc;
+  if (iters_per_case) {
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(t1.data(), s->S.iters_tot, nc * sizeof(long long), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(s, e, "batch_step");
+    for (int c = 0; c < nc; ++c) iters_per_case[c] = int32_t(t1[c] - t0[c]);
+  }
+  return rc;
+}
+
 int sisph_stats(sisph_t s, sisph_case_stats *st) {
   if (!valid_handle(s) || !st) return fail(s, SISPH_EINVAL, "invalid handle or stats");
   int nc = s->ncases;

@@ -96,6 +96,7 @@ def load_library(path: str = None):
         "sisph_compute_density": (C.c_int, [h]),
         "sisph_ppe_solve": (C.c_int, [h, C.c_double, C.c_int32, _ip, _dp]),
         "sisph_step": (C.c_int, [h, C.c_int32]),
+        "sisph_batch_step": (C.c_int, [h, C.c_int32, _ip]),
         "sisph_get": (C.c_int, [h, C.c_int32, _dp]),
         "sisph_set": (C.c_int, [h, C.c_int32, _dp]),
         "sisph_stats": (C.c_int, [h, C.POINTER(sisph_case_stats)]),
@@ -253,6 +254,14 @@ def sisph_neighbors(h, n):
     _check(L.sisph_neighbors(h, counts.ctypes.data_as(_ip), idx.ctypes.data_as(_ip), idx.size,
                              C.byref(tot)), h)
     return counts, idx[:tot.value]
+
+
+def sisph_batch_step(h, nsteps, ncases):
+    """Steps every case of a batch handle; returns (code, PPE sweeps per case)."""
+    its = np.zeros(ncases, np.int32)
+    rc = load_library().sisph_batch_step(h, int(nsteps), its.ctypes.data_as(_ip))
+    _check(rc, h, allow=(ENOTCONVERGED,))
+    return rc, its
 
 
 def sisph_stats(h, ncases):
