@@ -9,10 +9,12 @@
  *
  * Readings of passages that the paper leaves open are marked "Reading:".
  * Parity unpinned: the slip ghost velocity used for u* (or_ghost_velocity,
- * slip form), the 1e-6 length below which a smoothed wall normal is zero
- * (or_wall_normals) and the artificial-viscosity form (Monaghan's, read from
- * a garbled equation) have no value of their own to be checked against; the
- * hydrostatic, cavity and dam-break tests only exercise them.
+ * slip form) and the 1e-6 length below which a smoothed wall normal is zero
+ * (or_wall_normals) have no value of their own to be checked against; the
+ * hydrostatic, cavity and dam-break tests only exercise them.  The
+ * artificial-viscosity form (Monaghan's, read from a garbled equation) is
+ * pinned by its invariants only: momentum conservation, no force between
+ * receding pairs, and a force that opposes compression.
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared.
  */
 #include "sisph_oracle.h"
@@ -563,10 +565,10 @@ void or_stage1(or_sim *s) {
       for (int k = 0; k < 3; ++k) fi[k] += visc * uij[k];
       if (P->alpha > 0.0) {
         double vr = or_dot(uij, dx);
-        if (vr < 0.0) {
+        if (vr < 0.0 || g_plant == 7) {
           double phi = vr / (r2 + eh2);
           double pi_ij = -P->alpha * h * P->c0 * phi / (0.5 * (ri + rj));
-          for (int k = 0; k < 3; ++k) fi[k] -= mj * pi_ij * g[k];
+          for (int k = 0; k < 3; ++k) fi[k] -= ((g_plant == 8) ? -1.0 : 1.0) * mj * pi_ij * g[k];
         }
       }
       if (s->kind[j] == FLUID) {

@@ -236,3 +236,57 @@ def test_adaptive_time_step_tgv_first_step_is_cfl(oracle_lib):
     assert d[0].dt == case["params"]["dt"]
     assert abs(d[1].dt - 0.25 * h / umax0) <= 1e-13 * d[1].dt
     assert d[1].dt < 0.25 * h * h / case["params"]["nu"]
+
+
+def _moving_block(a, seed):
+    """A 12 x 12 block of fluid at lattice spacing (slightly perturbed) in an
+    open box, no walls, velocity u = a (r - r_c): dilating for a > 0."""
+    c = workloads.free_fall_blob(n_side=12, dx=0.05, spacing=1.0)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    c["x"] = c["x"] + rng.uniform(-0.005, 0.005, c["n"])
+    c["y"] = c["y"] + rng.uniform(-0.005, 0.005, c["n"])
+    xc, yc = c["x"].mean(), c["y"].mean()
+    c["u"] = a * (c["x"] - xc)
+    c["v"] = a * (c["y"] - yc)
+    return c, xc, yc
+
+
+def _avisc_only(c, **over):
+    # no viscosity, no gravity, transport velocity = u (no artificial stress):
+    # stage 1's force is the artificial viscosity alone
+    s = oracle.Sim(c, nu=0.0, g=(0.0, 0.0, 0.0), alpha=1.0, c0=10.0, adaptive_dt=0, **over)
+    s.set("ut", s.get("u"))
+    s.set("vt", s.get("v"))
+    s.stage1()
+    return s.get("fx"), s.get("fy")
+
+
+def test_artificial_viscosity_conserves_momentum(oracle_lib):
+    c = _random_periodic(24)
+    c["params"] = dict(c["params"], adaptive_dt=0)
+    fx, fy = _avisc_only(c)
+    m = c["m"]
+    assert np.abs(fx).max() > 0
+    assert abs(np.sum(m * fx)) < 1e-12 * np.sum(m * np.abs(fx))
+    assert abs(np.sum(m * fy)) < 1e-12 * np.sum(m * np.abs(fy))
+
+
+@pytest.mark.parametrize("plant", [0, 7, 8])
+def test_artificial_viscosity_acts_only_against_compression(oracle_lib, plant):
+    oracle.plant_mistake(plant)
+    try:
+        # dilation: every pair recedes (u_ij . r_ij > 0), no force at all
+        c, xc, yc = _moving_block(0.5, 31)
+        fx, fy = _avisc_only(c)
+        dilation_free = np.abs(fx).max() == 0.0 and np.abs(fy).max() == 0.0
+        # compression: the force pushes the particles apart (outward)
+        c, xc, yc = _moving_block(-0.5, 32)
+        fx, fy = _avisc_only(c)
+        outward = np.sum(fx * (c["x"] - xc) + fy * (c["y"] - yc))
+    finally:
+        oracle.plant_mistake(0)
+    if plant == 0:
+        assert dilation_free and outward > 0
+    else:
+        # 7 lets receding pairs feel it, 8 turns its sign
+        assert not (dilation_free and outward > 0)
