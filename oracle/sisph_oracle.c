@@ -8,10 +8,10 @@
  * with the CUDA library.
  *
  * Readings of passages that the paper leaves open are marked "Reading:".
- * Parity unpinned: the slip ghost velocity used for u* (or_ghost_velocity,
- * slip form) and the 1e-6 length below which a smoothed wall normal is zero
- * (or_wall_normals) have no value of their own to be checked against; the
- * hydrostatic, cavity and dam-break tests only exercise them.  The
+ * Parity unpinned: the 1e-6 length below which a smoothed wall normal is
+ * zero (or_wall_normals) has no value of its own to be checked against; the
+ * hydrostatic, cavity and dam-break tests only exercise it.  Both ghost
+ * velocity forms are pinned by a uniform flow along a resting floor.  The
  * artificial-viscosity form (Monaghan's, read from a garbled equation) is
  * pinned by its invariants only: momentum conservation, no force between
  * receding pairs, and a force that opposes compression.

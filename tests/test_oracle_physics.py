@@ -290,3 +290,41 @@ def test_artificial_viscosity_acts_only_against_compression(oracle_lib, plant):
     else:
         # 7 lets receding pairs feel it, 8 turns its sign
         assert not (dilation_free and outward > 0)
+
+
+@pytest.mark.parametrize("slip", [0, 1])
+def test_ghost_velocity_of_a_uniform_flow(oracle_lib, slip):
+    # fluid moving uniformly along the bottom wall of the still tank, U =
+    # (0.3, 0).  Slip form: the fluid's own velocity extended into the wall,
+    # so every wall that sees fluid carries U exactly (a Shepard mean of a
+    # constant).  No-slip form on the bottom wall away from the corners
+    # (normal +y, U tangential): 2 u_wall - U = -U, nothing into the solid.
+    # A wall with no fluid within the kernel's reach keeps u_wall = 0.
+    c = workloads.still_tank_2d(20, 20)
+    fl = c["kind"] == 0
+    c["u"] = np.where(fl, 0.3, 0.0)
+    c["v"] = np.zeros(c["n"])
+    s = oracle.Sim(c)
+    s.build_neighbors()
+    s.wall_normals()
+    s.ghost_velocity(slip)
+    ug, vg = s.get("ugx"), s.get("ugy")
+    h = c["params"]["h"]
+    reach = 3.0 * (h if slip else 0.5 * h)      # support of the Shepard kernel
+    pos = np.stack([c["x"], c["y"]], 1)
+    fpos = pos[fl]
+    dmin = np.array([np.sqrt(np.min(np.sum((fpos - p) ** 2, axis=1))) for p in pos])
+    walls = ~fl
+    sees = walls & (dmin < 0.99 * reach)
+    none = walls & (dmin >= reach)
+    assert np.count_nonzero(sees) > 20 and np.count_nonzero(none) > 5
+    if slip:
+        pick = sees
+        expect = 0.3
+    else:
+        pick = sees & (c["y"] < 0) & (c["x"] > 0.3) & (c["x"] < 0.7)
+        expect = -0.3
+        assert np.count_nonzero(pick) > 5
+    assert np.allclose(ug[pick], expect, rtol=0, atol=1e-12)
+    assert np.allclose(vg[pick], 0.0, rtol=0, atol=1e-12)
+    assert np.all(ug[none] == 0.0) and np.all(vg[none] == 0.0)
