@@ -380,9 +380,17 @@ __device__ __forceinline__ void count_empty_solves(const State &S) {
 // in the block's master thread followed by a block barrier, which orders
 // those reads after the other blocks' writes.  Flags and partial sums are
 // read with ld.global.cg.
+// A fluid row's slots go in chunks of CH: the chunk's index/coefficient
+// loads, then its CH gathers.  Longer chunks shorten the chain of dependent
+// loads behind each row (the tail of a phase waits for the longest chain),
+// fewer registers keep more blocks per SM to hide the latency of each load:
+// MIXED 3D rows (about 93 slots) take 16 at 4 blocks per SM, MIXED 2D rows
+// (25-45) 12 at 5, FP64 rows 8 at 4 (wider chunks would spill).
 // ---------------------------------------------------------------------------
-template <bool MX>
-__global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
+constexpr int sweep_blocks_per_sm(bool mx, int ch) { return !mx ? 4 : ch >= 16 ? 4 : ch >= 12 ? 5 : 8; }
+
+template <bool MX, int CH>
+__global__ void __launch_bounds__(256, sweep_blocks_per_sm(MX, CH)) k_sweeps(State S) {
   using R = typename std::conditional<MX, float, double>::type;
   __shared__ double sh[64];
   __shared__ int flag;
@@ -485,14 +493,14 @@ __global__ void __launch_bounds__(256, MX ? 8 : 4) k_sweeps(State S) {
         R acc = prhs[i];
         const int cnt = S.ncnt[i];
         const long long sb = slot_base(S, i);
-        for (int q0 = 0; q0 < cnt; q0 += 8) {
-          int jj[8];
-          R cf[8];
-          _Pragma("unroll") for (int u = 0; u < 8; ++u)
+        for (int q0 = 0; q0 < cnt; q0 += CH) {
+          int jj[CH];
+          R cf[CH];
+          _Pragma("unroll") for (int u = 0; u < CH; ++u)
             load_coef<R>(S, sb, q0 + u, q0 + u < cnt, i, jj[u], cf[u]);
-          R pj[8];
-          _Pragma("unroll") for (int u = 0; u < 8; ++u) pj[u] = pc[jj[u]];
-          _Pragma("unroll") for (int u = 0; u < 8; ++u) acc += cf[u] * pj[u];
+          R pj[CH];
+          _Pragma("unroll") for (int u = 0; u < CH; ++u) pj[u] = pc[jj[u]];
+          _Pragma("unroll") for (int u = 0; u < CH; ++u) acc += cf[u] * pj[u];
         }
         R po = pc[i];
         R pnew = pwd[i] * acc + om1 * po;
@@ -844,14 +852,20 @@ cudaError_t launch_ppe_setup(const State &S, const Launch &L) {
   return cudaGetLastError();
 }
 
+// The barrier-form kernel for the state's precision and dimension.
+using SweepKernel = void (*)(State);
+SweepKernel sweep_kernel(const State &S) {
+  if (!S.mixed) return k_sweeps<false, 8>;
+  return S.dim == 3 ? k_sweeps<true, 16> : k_sweeps<true, 12>;
+}
+
 int ppe_max_blocks_per_sm(const State &S, int block, bool p2p) {
   int nb = 0;
   if (p2p) {
     if (S.mixed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweeps_p2p<true>, block, 0);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweeps_p2p<false>, block, 0);
   } else {
-    if (S.mixed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweeps<true>, block, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweeps<false>, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel(S), block, 0);
   }
   return nb;
 }
@@ -898,8 +912,7 @@ cudaError_t launch_ppe_sweeps(const State &S, const Launch &L, int grid) {
     if (S.mixed) e = cudaLaunchKernelEx(&cfg, k_sweeps_p2p<true>, S);
     else e = cudaLaunchKernelEx(&cfg, k_sweeps_p2p<false>, S);
   } else {
-    if (S.mixed) e = cudaLaunchKernelEx(&cfg, k_sweeps<true>, S);
-    else e = cudaLaunchKernelEx(&cfg, k_sweeps<false>, S);
+    e = cudaLaunchKernelEx(&cfg, sweep_kernel(S), S);
   }
   if (L.after) L.after(L.ctx, "ppe_sweeps", 0.0, 1);
   return e;
