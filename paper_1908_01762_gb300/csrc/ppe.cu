@@ -380,8 +380,8 @@ __device__ __forceinline__ void count_empty_solves(const State &S) {
 // in the block's master thread followed by a block barrier, which orders
 // those reads after the other blocks' writes.  Flags and partial sums are
 // read with ld.global.cg.
-// A fluid row's slots go in chunks of CH: the chunk's index/coefficient
-// loads, then its CH gathers.  Longer chunks shorten the chain of dependent
+// A fluid row's slots (and a wall row's entries) go in chunks of CH: the
+// chunk's index/coefficient loads, then its CH gathers.  Longer chunks shorten the chain of dependent
 // loads behind each row (the tail of a phase waits for the longest chain),
 // fewer registers keep more blocks per SM to hide the latency of each load:
 // MIXED 3D rows (about 93 slots) take 16 at 4 blocks per SM, MIXED 2D rows
@@ -437,19 +437,19 @@ __global__ void __launch_bounds__(256, sweep_blocks_per_sm(MX, CH)) k_sweeps(Sta
         if (!bal && (!jacobi_case(S, c) || (k > 0 && __ldcg(done + c) && __ldcg(fin + c) != k))) continue;
         R acc = wh[r];
         const int cnt = S.wcnt[r];
-        for (int q0 = 0; q0 < cnt; q0 += 8) {
-          int jj[8];
-          R ww[8];
-          _Pragma("unroll") for (int u = 0; u < 8; ++u) {
+        for (int q0 = 0; q0 < cnt; q0 += CH) {
+          int jj[CH];
+          R ww[CH];
+          _Pragma("unroll") for (int u = 0; u < CH; ++u) {
             const int q = q0 + u;
             const long long o = ell_at(S.wcap, q, r);
             jj[u] = q < cnt ? S.widx[o] : w;
             ww[u] = q < cnt ? wc[o] : R(0);
             SISPH_CHECK_IDX(S, jj[u], w);
           }
-          R pv[8];
-          _Pragma("unroll") for (int u = 0; u < 8; ++u) pv[u] = pc[jj[u]];
-          _Pragma("unroll") for (int u = 0; u < 8; ++u) acc += ww[u] * pv[u];
+          R pv[CH];
+          _Pragma("unroll") for (int u = 0; u < CH; ++u) pv[u] = pc[jj[u]];
+          _Pragma("unroll") for (int u = 0; u < CH; ++u) acc += ww[u] * pv[u];
         }
         R pw = acc * wsinv[r];
         if (S.cases[c].free_surface && pw < R(0)) pw = R(0);
