@@ -3,8 +3,8 @@
 TEST INFRASTRUCTURE ONLY.  The oracle is a plain restatement of the SISPH
 time step (arXiv 1908.01762, Algorithm 1) used by the tests to check the CUDA
 library and by the benchmark's CPU-baseline leg.  The product path never
-imports this package.  Parity is unpinned for nothing here beyond what the
-oracle's C header lists; the pins live in ``tests/test_oracle_*.py``.
+imports this package.  The pins live in ``tests/test_oracle_*.py``; the
+oracle's C header lists which functions are pinned by invariants only.
 """
 from __future__ import annotations
 

@@ -8,10 +8,12 @@
  * with the CUDA library.
  *
  * Readings of passages that the paper leaves open are marked "Reading:".
- * Parity unpinned: the 1e-6 length below which a smoothed wall normal is
- * zero (or_wall_normals) has no value of its own to be checked against; the
- * hydrostatic, cavity and dam-break tests only exercise it.  Both ghost
- * velocity forms are pinned by a uniform flow along a resting floor.  The
+ * The wall normals are pinned by the symmetry of a three-layer wall (no
+ * normal on the middle layer, +-y on the others, the bisector at a corner);
+ * the two lengths below which a normal is taken as zero are readings whose
+ * exact values the paper does not fix: any value between rounding noise and
+ * the smallest real gradient gives the same normals.  Both ghost velocity
+ * forms are pinned by a uniform flow along a resting floor.  The
  * artificial-viscosity form (Monaghan's, read from a garbled equation) is
  * pinned by its invariants only: momentum conservation, no force between
  * receding pairs, and a force that opposes compression.
@@ -453,7 +455,8 @@ void or_wall_normals(or_sim *s) {
       for (int k = 0; k < 3; ++k) acc[k] -= vj * g[k];
     }
     double mag = sqrt(or_dot(acc, acc));
-    for (int k = 0; k < 3; ++k) ns[k][i] = (mag < 1.0 / (4.0 * h)) ? 0.0 : acc[k] / mag;
+    const int keep = g_plant == 10 ? mag > 0.0 : mag >= 1.0 / (4.0 * h);
+    for (int k = 0; k < 3; ++k) ns[k][i] = keep ? acc[k] / mag : 0.0;
   }
   for (int64_t i = 0; i < n; ++i) {
     for (int k = 0; k < 3; ++k) s->nrm[k][i] = 0.0;
@@ -468,7 +471,7 @@ void or_wall_normals(or_sim *s) {
       for (int k = 0; k < 3; ++k) acc[k] += wv * ns[k][j];
     }
     double mag = sqrt(or_dot(acc, acc));
-    if (mag > 1e-6)
+    if (mag > 1e-6 || (g_plant == 9 && mag > 0.0))
       for (int k = 0; k < 3; ++k) s->nrm[k][i] = acc[k] / mag;
   }
   for (int k = 0; k < 3; ++k) free(ns[k]);

@@ -190,6 +190,47 @@ def test_flat_wall_normals(oracle_lib):
     assert np.all((np.abs(mag - 1) < 1e-12) | (mag == 0))
 
 
+def _layer_normals():
+    # resting tank with three wall layers (dx = 0.1): the bottom layers sit at
+    # y = -0.05, -0.15, -0.25 and the left ones at x = -0.05, -0.15, -0.25
+    c = workloads.still_tank_2d(12, 12, dx=0.1)
+    s = oracle.Sim(c)
+    x, y, wall = c["x"], c["y"], c["kind"] == 1
+    mid = (x > 0.4) & (x < 0.8)
+    layer = {k: wall & np.isclose(y, yy) & mid for k, yy in (("inner", -0.05), ("middle", -0.15), ("outer", -0.25))}
+    corner = wall & np.isclose(x, -0.05) & np.isclose(y, -0.05)
+    return s.get("nx"), s.get("ny"), layer, corner
+
+
+def _check_layer_normals(nx, ny, layer, corner):
+    # the middle layer sees one layer on either side at the same distance: its
+    # raw gradient sum cancels (below the zero threshold) and so does the
+    # smoothed sum of the inner (+y) and outer (-y) normals, so it has none
+    assert np.all(nx[layer["middle"]] == 0.0) and np.all(ny[layer["middle"]] == 0.0)
+    # the inner layer points into the tank, the outer layer away from the solid
+    assert np.allclose(ny[layer["inner"]], 1.0, rtol=0, atol=1e-12)
+    assert np.allclose(ny[layer["outer"]], -1.0, rtol=0, atol=1e-12)
+    # the inner corner particle is symmetric about the diagonal: the bisector
+    assert corner.sum() == 1
+    assert np.allclose(nx[corner], math.sqrt(0.5), rtol=0, atol=1e-12)
+    assert np.allclose(ny[corner], math.sqrt(0.5), rtol=0, atol=1e-12)
+
+
+def test_wall_normals_of_symmetric_layers(oracle_lib):
+    """Eqs. normal-approx, normal: geometry fixes the normals of a three-layer
+    wall -- none on the middle layer, whose neighbourhood is symmetric, +-y on
+    the inner and outer layers, the diagonal at the inner corner."""
+    _check_layer_normals(*_layer_normals())
+
+
+@pytest.mark.parametrize("plant", [9, 10])
+def test_planted_normal_thresholds_are_caught(oracle_lib, plant):
+    # 9: the smoothed normal normalised however small; 10: the raw one
+    oracle.plant_mistake(plant)
+    with pytest.raises(AssertionError):
+        _check_layer_normals(*_layer_normals())
+
+
 def test_adaptive_time_step_in_free_fall(oracle_lib):
     """Adaptive dt (Sec. 3.2) against the closed form of a free fall: the only
     force is g, so max|f| = g and max|u^n| = g t_n.  The step after one
