@@ -219,12 +219,33 @@ def kernel_bytes(site, mixed, dim, n_f, n, s_f, s_all, ss_all):
 LIVE_SITES = [k for k in SITES if k not in ("sort", "build")]
 
 
+def launch_options(args, cases, prec):
+    """Launch shapes of the run (tile size, Verlet skin, sweep form) and a
+    note of where they come from: the autotuner's cached choice for this
+    workload class on this GPU (--tune cache, the default), a tuning run now
+    whose result is merged into --tune-cache (--tune run), or the library's
+    defaults (--tune off)."""
+    from paper_1908_01762_gb300 import autotune
+    if args.tune == "off":
+        return {}, {"source": "library defaults"}
+    if args.tune == "run":
+        entry = autotune.tune(cases, prec, steps=args.tune_steps, path=args.tune_cache,
+                              log=lambda m: print(m, file=sys.stderr, flush=True))
+        return dict(entry["options"]), {"source": "tuned in this run", **entry["options"],
+                                        "tuned_ms_per_step": entry["ms_per_step"],
+                                        "default_ms_per_step": entry["default_ms_per_step"]}
+    opts = autotune.lookup(cases, prec, args.tune_cache)
+    if opts is None:
+        return {}, {"source": "library defaults (no autotune entry for this workload class)"}
+    return opts, {"source": "autotune cache", **opts}
+
+
 def site_times(sisph, cases, prec, args, flush, stream):
     """Device time per step of every live site over the same steps as the
     timed region (L2 flushed between steps alike), on a replica of the
     simulation -- the run is deterministic, so the steps are identical -- so
     that the timed run itself carries events on one kernel only."""
-    sim = sisph.Simulation(cases, precision=prec, use_graph=1)
+    sim = sisph.Simulation(cases, precision=prec, use_graph=1, **args.launch_opts)
     sisph.sisph_set_stream(sim.h, stream.cuda_stream)
     sisph.sisph_profile_enable(sim.h, True, ",".join(LIVE_SITES))
     for _ in range(args.warmup):
@@ -278,6 +299,7 @@ def run_ours(args, rank, world):
     dim = cases[0]["dim"]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    args.launch_opts, launch_note = launch_options(args, cases, prec)
 
     # per-site device time per step over the same steps, on an identical
     # replica; the dominant kernel with a byte model is then timed live in
@@ -290,7 +312,8 @@ def run_ours(args, rank, world):
         modeled = [k for k in sites if k == "ppe_sweeps" or kernel_bytes(k, mixed, dim, 1, 1, 1, 1, 1)]
         roof_site = max(modeled, key=lambda k: sites[k]["ms_per_step"])
 
-    sim = sisph.Simulation(cases, precision=prec, use_graph=0 if args.no_graph else 1)
+    sim = sisph.Simulation(cases, precision=prec, use_graph=0 if args.no_graph else 1,
+                           **args.launch_opts)
     sisph.sisph_set_stream(sim.h, stream.cuda_stream)
     n = sim.n
     kinds = np.concatenate([c["kind"] for c in cases])
@@ -379,7 +402,7 @@ def run_ours(args, rank, world):
                    "cases": len(cases), "precision": args.precision,
                    "ppe_sweeps_per_step": iters_per_step, "l2": "flushed between steps (256 MiB write)",
                    "graph": "direct launches" if args.no_graph else "CUDA graph replay per step",
-                   "parallelism": f"replicas{world}",
+                   "parallelism": f"replicas{world}", "launch": launch_note,
                    "neighbour_rebuilds_per_refresh": float(np.mean(rebuilds)) / (2 * args.steps)},
         "ppe_interactions_per_s": world * pairs / (t_ms * 1e-3),
         "roofline": {"kernel": roof_site, "bound": "hbm",
@@ -557,7 +580,7 @@ def step_log(args, path):
     from paper_1908_01762_gb300 import sisph
     cases, _ = make_workload(args.workload)
     prec = sisph.MIXED if args.precision == "mixed" else sisph.FP64
-    sim = sisph.Simulation(cases, precision=prec, use_graph=1)
+    sim = sisph.Simulation(cases, precision=prec, use_graph=1, **getattr(args, "launch_opts", {}))
     stream = torch.cuda.current_stream()
     sisph.sisph_set_stream(sim.h, stream.cuda_stream)
     dim = cases[0]["dim"]
@@ -715,9 +738,18 @@ def main():
     ap.add_argument("--log", default=None,
                     help="also write a per-step JSONL record (sweeps, residual, Lambda, max |u|, "
                          "neighbour counts) of a replica run to this file")
+    ap.add_argument("--tune", choices=["cache", "run", "off"], default="cache",
+                    help="launch shapes: the autotuner's cached choice for this workload class "
+                         "on this GPU (default), tune now and merge into --tune-cache, or the "
+                         "library defaults")
+    ap.add_argument("--tune-cache", default=None,
+                    help="autotune cache file (default: the one shipped with the package)")
+    ap.add_argument("--tune-steps", type=int, default=30, help="timed steps per tuning candidate")
     ap.add_argument("--study", choices=["tolerance", "solver", "batch", "eisph"], default=None,
                     help="run a parameter study instead of the benchmark")
     args = ap.parse_args()
+    if args.tune_cache is None:
+        args.tune_cache = os.path.join(ROOT, "paper_1908_01762_gb300", "autotune_gb300.json")
     if args.steps is None:
         # the batch's high-Re Taylor-Green members start clustering after
         # about 150 steps at eps = 1e-2 (the oracle does the same) and then
