@@ -744,7 +744,8 @@ def main():
                          "library defaults")
     ap.add_argument("--tune-cache", default=None,
                     help="autotune cache file (default: the one shipped with the package)")
-    ap.add_argument("--tune-steps", type=int, default=30, help="timed steps per tuning candidate")
+    ap.add_argument("--tune-steps", type=int, default=None,
+                    help="timed steps per tuning candidate (default: --steps)")
     ap.add_argument("--study", choices=["tolerance", "solver", "batch", "eisph"], default=None,
                     help="run a parameter study instead of the benchmark")
     args = ap.parse_args()
@@ -755,6 +756,8 @@ def main():
         # about 150 steps at eps = 1e-2 (the oracle does the same) and then
         # overflow the neighbour capacity; every timed run starts at t = 0
         args.steps = 100 if args.workload == "c5" else 200
+    if args.tune_steps is None:
+        args.tune_steps = args.steps
     if args.study == "tolerance":
         study_tolerance(args)
         return

@@ -10,9 +10,10 @@ means fewer rebuilds but longer lists to filter at every refresh; the
 point-to-point sweeps save the grid barriers only while every block owns one
 tile.
 
-`tune` times a few graph-replayed steps of the caller's own workload (L2
-flushed between steps, CUDA events on the library's stream) for every
-candidate and keeps the fastest.  Results are cached in a JSON file per GPU
+`tune` times graph-replayed steps of the caller's own workload (L2 flushed
+between steps, CUDA events on the library's stream; as many steps as the run
+to be tuned, since the PPE's sweep count changes as a flow develops) for every
+candidate and keeps the fastest, unless it beats the defaults by less than 1 %.  Results are cached in a JSON file per GPU
 model and workload class (dimension, precision, case count and total size to
 within a factor of about 1.4, walls or not); `lookup` returns the cached
 options for a workload of the same class.  The package ships the cache tuned
@@ -118,12 +119,18 @@ def time_options(cases, precision, opts, steps, warmup, flush, stream):
         sim.close()
 
 
-def pick(trials):
-    """The fastest trial that ran; ties keep the earlier candidate."""
+def pick(trials, margin=0.01):
+    """The fastest trial that ran (ties keep the earlier one), unless it is
+    less than `margin` faster than the first trial (the defaults): a gain
+    within run-to-run noise does not move the choice off the defaults."""
     ok = [t for t in trials if t["ms_per_step"] is not None]
     if not ok:
         raise RuntimeError("no candidate ran")
-    return min(ok, key=lambda t: t["ms_per_step"])
+    best = min(ok, key=lambda t: t["ms_per_step"])
+    first = trials[0]
+    if first["ms_per_step"] is not None and best["ms_per_step"] > first["ms_per_step"] * (1.0 - margin):
+        return first
+    return best
 
 
 def tune(cases, precision, steps=30, warmup=3, path=None, log=None, timer=None, device=None,

@@ -45,6 +45,12 @@ def test_pick():
     t = [{"options": {"a": 0}, "ms_per_step": 2.0}, {"options": {"a": 1}, "ms_per_step": None},
          {"options": {"a": 2}, "ms_per_step": 1.5}, {"options": {"a": 3}, "ms_per_step": 1.5}]
     assert autotune.pick(t)["options"] == {"a": 2}
+    # within 1 % of the defaults (the first trial): the defaults stay
+    near = [{"options": {"a": 0}, "ms_per_step": 1.0}, {"options": {"a": 1}, "ms_per_step": 0.995}]
+    assert autotune.pick(near)["options"] == {"a": 0}
+    assert autotune.pick(near, margin=0.0)["options"] == {"a": 1}
+    # defaults that cannot run: the fastest of the rest
+    assert autotune.pick([{"options": {"a": 0}, "ms_per_step": None}] + near[1:])["options"] == {"a": 1}
     with pytest.raises(RuntimeError):
         autotune.pick([{"options": {}, "ms_per_step": None}])
 
@@ -82,4 +88,5 @@ def test_shipped_cache_is_valid():
         assert o["block"] % 32 == 0 and 64 <= o["block"] <= 256
         assert 0.0 <= o["skin"] <= 1.0 and o["ppe_sync"] in (0, 1, 2)
         assert e["ms_per_step"] <= e["default_ms_per_step"]
+        assert e["options"] == autotune.DEFAULTS or e["ms_per_step"] < 0.99 * e["default_ms_per_step"]
         assert any(t["options"] == o and t["ms_per_step"] == e["ms_per_step"] for t in e["trials"])

@@ -51,5 +51,7 @@ def test_tune_writes_and_looks_up(sisph, tmp_path):
     path = str(tmp_path / "tune.json")
     e = autotune.tune([case], sisph.MIXED, steps=3, warmup=3, path=path)
     assert all(t["ms_per_step"] is not None and t["ms_per_step"] > 0 for t in e["trials"])
-    assert e["ms_per_step"] == min(t["ms_per_step"] for t in e["trials"])
+    best = min(t["ms_per_step"] for t in e["trials"])
+    assert e["ms_per_step"] == best or (e["options"] == autotune.DEFAULTS
+                                        and best > 0.99 * e["ms_per_step"])
     assert autotune.lookup([case], sisph.MIXED, path) == e["options"]
