@@ -14,6 +14,11 @@ Timed steps are bracketed by CUDA events on the library's stream, with a
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload c1|c2|c3|c4|c4l|c5] [--precision mixed|fp64]
+                    [--tune cache|run|off]
+
+Launch shapes (tile size, Verlet skin, sweep form) come from the autotuner's
+cache shipped with the package for this GPU model and workload class, else
+the library's defaults; the line names them in config.launch.
 
 With N > 1 (torchrun) every rank runs its own replica ("replicas only": one
 case does not shard without a halo exchange); the line reports the total
