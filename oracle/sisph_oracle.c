@@ -13,7 +13,9 @@
  * the two lengths below which a normal is taken as zero are readings whose
  * exact values the paper does not fix: any value between rounding noise and
  * the smallest real gradient gives the same normals.  Both ghost velocity
- * forms are pinned by a uniform flow along a resting floor.  The
+ * forms are pinned by a uniform flow along a resting floor, the artificial
+ * stress by the divergence of a linear tensor field and by momentum
+ * conservation.  The
  * artificial-viscosity form (Monaghan's, read from a garbled equation) is
  * pinned by its invariants only: momentum conservation, no force between
  * receding pairs, and a force that opposes compression.
@@ -577,8 +579,13 @@ void or_stage1(or_sim *s) {
       if (s->kind[j] == FLUID) {
         double dti[3] = {s->ut[0][i] - ui[0], s->ut[1][i] - ui[1], s->ut[2][i] - ui[2]};
         double dtj[3] = {s->ut[0][j] - uj[0], s->ut[1][j] - uj[1], s->ut[2][j] - uj[2]};
-        double ai = or_dot(dti, g) / ri, aj = or_dot(dtj, g) / rj;
-        for (int k = 0; k < 3; ++k) fi[k] += mj * (ui[k] * ai + uj[k] * aj);
+        if (g_plant == 11) {            /* planted: the tensor transposed */
+          double ai = or_dot(ui, g) / ri, aj = or_dot(uj, g) / rj;
+          for (int k = 0; k < 3; ++k) fi[k] += mj * (dti[k] * ai + dtj[k] * aj);
+        } else {
+          double ai = or_dot(dti, g) / ri, aj = (g_plant == 12) ? 0.0 : or_dot(dtj, g) / rj;
+          for (int k = 0; k < 3; ++k) fi[k] += mj * (ui[k] * ai + uj[k] * aj);
+        }
       }
     }
     for (int k = 0; k < 3; ++k) {

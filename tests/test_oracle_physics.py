@@ -333,6 +333,59 @@ def test_artificial_viscosity_acts_only_against_compression(oracle_lib, plant):
         assert not (dilation_free and outward > 0)
 
 
+def _astress_only(c, ut, vt):
+    # no viscosity, no artificial viscosity, no gravity: stage 1's force is the
+    # artificial stress alone (Eq. mom:sph:gtvf:stress)
+    s = oracle.Sim(c, nu=0.0, g=(0.0, 0.0, 0.0), alpha=0.0, adaptive_dt=0)
+    s.set("ut", ut)
+    s.set("vt", vt)
+    s.stage1()
+    return s.get("fx"), s.get("fy")
+
+
+def _stress_of_a_linear_field():
+    """A 24 x 24 lattice block (h = dx, uniform rho), u = (U, 0) and
+    u~ - u = (0, beta y): A = rho u (x) (u~ - u) has the one entry
+    A_xy = rho U beta y, so (1/rho) div A = (U beta, 0).  The symmetric SPH
+    form is that divergence for particles whose support lies inside the
+    block."""
+    U, beta = 0.7, 3.0
+    c = workloads.free_fall_blob(n_side=24, dx=0.05, spacing=1.0, adaptive=False)
+    c["u"] = np.full(c["n"], U)
+    c["v"] = np.zeros(c["n"])
+    yc = c["y"].mean()
+    fx, fy = _astress_only(c, c["u"], beta * (c["y"] - yc))
+    h = c["params"]["h"]
+    x, y = c["x"], c["y"]
+    inner = ((x - x.min() > 6 * h) & (x.max() - x > 6 * h) & (y - y.min() > 6 * h)
+             & (y.max() - y > 6 * h))
+    assert inner.sum() >= 100
+    return fx[inner], fy[inner], U * beta
+
+
+@pytest.mark.parametrize("plant", [0, 11, 12])
+def test_artificial_stress_of_a_linear_field(oracle_lib, plant):
+    oracle.plant_mistake(plant)
+    try:
+        fx, fy, expect = _stress_of_a_linear_field()
+    finally:
+        oracle.plant_mistake(0)
+    ok = np.allclose(fx, expect, rtol=2e-3, atol=0) and np.all(fy == 0.0)
+    # 11 transposes the tensor (u~ - u) (x) u, 12 drops the neighbour's A_j
+    assert ok == (plant == 0)
+
+
+def test_artificial_stress_conserves_momentum(oracle_lib):
+    c = _random_periodic(25)
+    c["params"] = dict(c["params"], adaptive_dt=0)
+    rng = np.random.Generator(np.random.PCG64(26))
+    fx, fy = _astress_only(c, c["u"] + rng.normal(0, 0.3, c["n"]), c["v"] + rng.normal(0, 0.3, c["n"]))
+    m = c["m"]
+    assert np.abs(fx).max() > 0
+    assert abs(np.sum(m * fx)) < 1e-12 * np.sum(m * np.abs(fx))
+    assert abs(np.sum(m * fy)) < 1e-12 * np.sum(m * np.abs(fy))
+
+
 @pytest.mark.parametrize("slip", [0, 1])
 def test_ghost_velocity_of_a_uniform_flow(oracle_lib, slip):
     # fluid moving uniformly along the bottom wall of the still tank, U =
