@@ -424,6 +424,7 @@ void or_density(or_sim *s) {
     double acc = 0.0;
     for (int64_t t = s->nstart[i]; t < s->nstart[i + 1]; ++t) {
       int64_t j = s->nidx[t];
+      if (g_plant == 13 && s->kind[j] != FLUID) continue;   /* planted: walls left out */
       double dx[3];
       double r2 = or_pair(&s->prm, (const double *const *)s->x, i, j, dx);
       acc += s->m[j] * or_kernel_w(sqrt(r2), s->prm.h, s->prm.dim);
@@ -643,7 +644,7 @@ void or_ppe_setup(or_sim *s) {
       }
       s->rhs[i] = rhs;
       s->diag[i] = dg;
-      int fs = P->free_surface && (ri / P->rho0 < P->fs_ratio);
+      int fs = P->free_surface && (ri / P->rho0 < P->fs_ratio) && g_plant != 14;
       s->active[i] = (dg != 0.0) && !fs;
       if (!s->active[i]) s->p[i] = 0.0;
       else {

@@ -333,6 +333,62 @@ def test_artificial_viscosity_acts_only_against_compression(oracle_lib, plant):
         assert not (dilation_free and outward > 0)
 
 
+def _tank_density():
+    # resting tank: fluid lattice continued by three wall layers on the same
+    # lattice (m_w = rho0 dx^2); every fluid particle whose support stays
+    # below the free surface sees a complete lattice, walls included
+    c = workloads.still_tank_2d(16, 16)
+    s = oracle.Sim(c)
+    s.density()
+    rho = s.get("rho") / c["params"]["rho0"]
+    fl = c["kind"] == 0
+    h = c["params"]["h"]
+    deep = fl & (c["y"] < c["y"][fl].max() - 3 * h)
+    near_wall = deep & ((c["y"] < 3 * h) | (c["x"] < 3 * h))
+    return rho, deep, near_wall
+
+
+@pytest.mark.parametrize("plant", [0, 13])
+def test_summation_density_of_a_lattice_with_walls(oracle_lib, plant):
+    """Eq. summation_density over fluid and wall neighbours (reading 9): on a
+    lattice the sum is rho0 times the lattice partition of unity, 1.00006322
+    for the 2D quintic at h = dx, also next to the walls."""
+    oracle.plant_mistake(plant)
+    try:
+        rho, deep, near_wall = _tank_density()
+    finally:
+        oracle.plant_mistake(0)
+    assert near_wall.sum() > 20
+    ok = np.allclose(rho[deep], 1.00006322, rtol=0, atol=1e-8)
+    # 13 leaves the walls out of the fluid's sums
+    assert ok == (plant == 0)
+
+
+@pytest.mark.parametrize("plant", [0, 14])
+def test_free_surface_particles_keep_zero_pressure(oracle_lib, plant):
+    """Sec. 3: fluid below 0.8 rho0 (the top rows of a resting tank, whose
+    support reaches above the surface) is a Dirichlet row p = 0 -- the
+    surface value of the hydrostatic p = rho0 g (H - y) -- while the deep
+    fluid carries the hydrostatic pressure."""
+    c = workloads.still_tank_2d(16, 16)
+    oracle.plant_mistake(plant)
+    try:
+        s = oracle.Sim(c)
+        s.density()
+        s.ppe_solve(1e-6, 5000)
+        p, rho = s.get("p"), s.get("rho") / c["params"]["rho0"]
+    finally:
+        oracle.plant_mistake(0)
+    fl = c["kind"] == 0
+    top = fl & (rho < 0.8)
+    h = c["params"]["h"]
+    deep = fl & (c["y"] < c["y"][fl].max() - 3 * h)
+    assert 16 <= top.sum() <= 48 and deep.sum() > 150
+    ok = np.all(p[top] == 0.0) and np.all(p[deep] > 0.0)
+    # 14 solves the surface rows like interior ones
+    assert ok == (plant == 0)
+
+
 def _astress_only(c, ut, vt):
     # no viscosity, no artificial viscosity, no gravity: stage 1's force is the
     # artificial stress alone (Eq. mom:sph:gtvf:stress)
