@@ -1,9 +1,7 @@
 """Host logic of the launch-shape autotuner: cache keys, candidates, the
 choice, the cache file and the shipped GB300 entries (no GPU)."""
 import json
-import os
 
-import numpy as np
 import pytest
 
 import workloads
