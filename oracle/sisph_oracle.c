@@ -19,7 +19,7 @@
  * artificial-viscosity form (Monaghan's, read from a garbled equation) is
  * pinned by its invariants only: momentum conservation, no force between
  * receding pairs, and a force that opposes compression.
- * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared.
+ * Build: gcc -O2 -std=c11 -D_GNU_SOURCE (for M_PI) -ffp-contract=off -fPIC -shared.
  */
 #include "sisph_oracle.h"
 

@@ -667,9 +667,9 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
     if (e == cudaSuccess) e = dalloc(s, p, cnt);
   };
   const size_t N = size_t(ntot);
-  CaseDev *dcases;
-  Tile *dft, *dwt;
-  int *dcase_of, *dwall_at;
+  CaseDev *dcases = nullptr;
+  Tile *dft = nullptr, *dwt = nullptr;
+  int *dcase_of = nullptr, *dwall_at = nullptr;
   A(&dcases, ncases);
   A(&dft, std::max(1, S.nft));
   A(&dwt, std::max(1, S.nwt));
