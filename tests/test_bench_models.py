@@ -49,3 +49,24 @@ def test_traffic_summaries_are_read_only_for_the_kernel_they_measured(path):
     else:
         assert got is None        # the kernel changed since the counters were taken
     assert bench.measured_traffic(workload, site, 0.0) is None
+
+
+def test_launch_options_follow_the_tune_flag(tmp_path, monkeypatch):
+    import argparse
+    import workloads
+    from paper_1908_01762_gb300 import autotune, sisph
+    monkeypatch.setattr(autotune, "device_name", lambda: "GPU sm_103 x152")
+    cases = [workloads.taylor_green(50)]
+    path = str(tmp_path / "cache.json")
+    args = argparse.Namespace(tune="off", tune_cache=path, tune_steps=5)
+    assert bench.launch_options(args, cases, sisph.MIXED) == ({}, {"source": "library defaults"})
+    args.tune = "cache"
+    opts, note = bench.launch_options(args, cases, sisph.MIXED)
+    assert opts == {} and note["source"].startswith("library defaults")
+    autotune.tune(cases, sisph.MIXED, path=path, device="GPU sm_103 x152", sms=152,
+                  timer=lambda o: 1.0 if o["block"] == 128 and o["skin"] == 0.1 else 2.0)
+    opts, note = bench.launch_options(args, cases, sisph.MIXED)
+    assert opts == {"block": 128, "skin": 0.1, "ppe_sync": 0}
+    assert note == {"source": "autotune cache", **opts}
+    # the shipped cache is what the benchmark reads by default
+    assert os.path.dirname(autotune.DEFAULT_CACHE) == os.path.join(ROOT, "paper_1908_01762_gb300")
