@@ -1080,7 +1080,7 @@ int32_t or_step(or_sim *s, int32_t nsteps, or_diag *d) {
     memset(&dd, 0, sizeof(dd));
     if (s->prm.ppe_solver == 1) or_ppe_bicgstab(s, &dd);
     else or_ppe_iterate(s, &dd);
-    if (!s->pref_set) {
+    if (!s->pref_set || g_plant == 15) {   /* planted 15: p_ref re-taken every step */
       double mx = 0.0;
       int first = 1;
       for (int64_t i = 0; i < s->n; ++i)

@@ -389,6 +389,27 @@ def test_free_surface_particles_keep_zero_pressure(oracle_lib, plant):
     assert ok == (plant == 0)
 
 
+@pytest.mark.parametrize("plant", [0, 15])
+def test_reference_pressure_of_the_taylor_green_vortex(oracle_lib, plant):
+    """Internal flows take p_ref = 2 max_i p_i from the first solve and keep
+    it (reading 16).  The vortex's pressure -rho U^2/4 (cos 4 pi x + cos 4 pi y)
+    e^{2bt} peaks at rho U^2 / 2, so p_ref is rho U^2 = 1 to the method's
+    accuracy after one step."""
+    c = workloads.taylor_green(50)
+    oracle.plant_mistake(plant)
+    try:
+        s = oracle.Sim(c)
+        s.step(1)
+        p1 = s.p_ref
+        s.step(1)
+        p2 = s.p_ref
+    finally:
+        oracle.plant_mistake(0)
+    assert abs(p1 - 1.0) < 0.01
+    # 15 takes p_ref again after every solve
+    assert (p2 == p1) == (plant == 0)
+
+
 def _astress_only(c, ut, vt):
     # no viscosity, no artificial viscosity, no gravity: stage 1's force is the
     # artificial stress alone (Eq. mom:sph:gtvf:stress)
