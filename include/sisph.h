@@ -118,7 +118,8 @@ typedef struct {
                                    fluid particle of the case moved more than s/2
                                    since the last rebuild, and filtered exactly to
                                    N(i) at every refresh; 0 rebuilds every time */
-  int32_t block;                /* threads per block / tile size (64..1024, mult. of 32) */
+  int32_t block;                /* threads per block / tile size (64..256, mult. of 32;
+                                   256 by default, autotune.py may pick 128) */
   int32_t use_graph;            /* capture sisph_step in a CUDA graph and replay it */
   double barrier_timeout_ms;    /* budget of one grid-barrier wait */
   int32_t debug_skip_barrier;   /* test hook: block 1 skips its first barrier arrival */
