@@ -18,9 +18,6 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sisph_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-_lib = None
-
-
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2, no fused multiply-add)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
@@ -53,49 +50,61 @@ class Diag(C.Structure):
                 ("dt", C.c_double)]
 
 
+_libs = {}        # mistake number (0: none) -> loaded library
+_active = 0       # the library lib() returns (a planted mistake, or 0)
+
+
+def _declare(L):
+    dp = C.POINTER(C.c_double)
+    ip = C.POINTER(C.c_int32)
+    L.or_default_params.argtypes = [C.POINTER(Params)]
+    L.or_kernel_w.argtypes = [C.c_double, C.c_double, C.c_int32]
+    L.or_kernel_w.restype = C.c_double
+    L.or_kernel_dwdr.argtypes = [C.c_double, C.c_double, C.c_int32]
+    L.or_kernel_dwdr.restype = C.c_double
+    L.or_neighbors.argtypes = [C.POINTER(Params), C.c_int64, dp, dp, dp, ip, ip, C.c_int64]
+    L.or_neighbors.restype = C.c_int64
+    L.or_create.argtypes = [C.POINTER(Params), C.c_int64] + [dp] * 9 + [ip] + [dp] * 3
+    L.or_create.restype = C.c_void_p
+    L.or_destroy.argtypes = [C.c_void_p]
+    L.or_get.argtypes = [C.c_void_p, C.c_char_p, dp]
+    L.or_get.restype = C.c_int32
+    L.or_set.argtypes = [C.c_void_p, C.c_char_p, dp]
+    L.or_set.restype = C.c_int32
+    L.or_build_neighbors.argtypes = [C.c_void_p]
+    L.or_build_neighbors.restype = C.c_int64
+    L.or_neighbor_list.argtypes = [C.c_void_p, ip, ip, C.c_int64]
+    L.or_neighbor_list.restype = C.c_int64
+    for fn in ("or_density", "or_wall_normals", "or_stage1", "or_ppe_setup",
+               "or_pressure_gradient", "or_gtvf", "or_update"):
+        getattr(L, fn).argtypes = [C.c_void_p]
+    L.or_ghost_velocity.argtypes = [C.c_void_p, C.c_int32]
+    L.or_ppe_iterate.argtypes = [C.c_void_p, C.POINTER(Diag)]
+    L.or_ppe_apply.argtypes = [C.c_void_p, dp, dp]
+    L.or_ppe_export.argtypes = [C.c_void_p, dp, dp, ip, dp, dp, dp, dp]
+    L.or_ppe_export.restype = C.c_int64
+    L.or_step.argtypes = [C.c_void_p, C.c_int32, C.POINTER(Diag)]
+    L.or_step.restype = C.c_int32
+    L.or_ppe_solve.argtypes = [C.c_void_p, C.c_double, C.c_int32, C.POINTER(Diag)]
+    L.or_ppe_solve.restype = C.c_int32
+    L.or_get_pref.argtypes = [C.c_void_p]
+    L.or_get_pref.restype = C.c_double
+    L.or_get_dt.argtypes = [C.c_void_p]
+    L.or_get_dt.restype = C.c_double
+    return L
+
+
 def lib():
-    global _lib
-    if _lib is None:
-        _lib = C.CDLL(build())
-        L = _lib
-        dp = C.POINTER(C.c_double)
-        ip = C.POINTER(C.c_int32)
-        L.or_default_params.argtypes = [C.POINTER(Params)]
-        L.or_kernel_w.argtypes = [C.c_double, C.c_double, C.c_int32]
-        L.or_kernel_w.restype = C.c_double
-        L.or_kernel_dwdr.argtypes = [C.c_double, C.c_double, C.c_int32]
-        L.or_kernel_dwdr.restype = C.c_double
-        L.or_neighbors.argtypes = [C.POINTER(Params), C.c_int64, dp, dp, dp, ip, ip, C.c_int64]
-        L.or_neighbors.restype = C.c_int64
-        L.or_create.argtypes = [C.POINTER(Params), C.c_int64] + [dp] * 9 + [ip] + [dp] * 3
-        L.or_create.restype = C.c_void_p
-        L.or_destroy.argtypes = [C.c_void_p]
-        L.or_get.argtypes = [C.c_void_p, C.c_char_p, dp]
-        L.or_get.restype = C.c_int32
-        L.or_set.argtypes = [C.c_void_p, C.c_char_p, dp]
-        L.or_set.restype = C.c_int32
-        L.or_build_neighbors.argtypes = [C.c_void_p]
-        L.or_build_neighbors.restype = C.c_int64
-        L.or_neighbor_list.argtypes = [C.c_void_p, ip, ip, C.c_int64]
-        L.or_neighbor_list.restype = C.c_int64
-        for fn in ("or_density", "or_wall_normals", "or_stage1", "or_ppe_setup",
-                   "or_pressure_gradient", "or_gtvf", "or_update"):
-            getattr(L, fn).argtypes = [C.c_void_p]
-        L.or_ghost_velocity.argtypes = [C.c_void_p, C.c_int32]
-        L.or_ppe_iterate.argtypes = [C.c_void_p, C.POINTER(Diag)]
-        L.or_ppe_apply.argtypes = [C.c_void_p, dp, dp]
-        L.or_ppe_export.argtypes = [C.c_void_p, dp, dp, ip, dp, dp, dp, dp]
-        L.or_ppe_export.restype = C.c_int64
-        L.or_step.argtypes = [C.c_void_p, C.c_int32, C.POINTER(Diag)]
-        L.or_step.restype = C.c_int32
-        L.or_ppe_solve.argtypes = [C.c_void_p, C.c_double, C.c_int32, C.POINTER(Diag)]
-        L.or_ppe_solve.restype = C.c_int32
-        L.or_get_pref.argtypes = [C.c_void_p]
-        L.or_get_pref.restype = C.c_double
-        L.or_get_dt.argtypes = [C.c_void_p]
-        L.or_get_dt.restype = C.c_double
-        L.or_plant_mistake.argtypes = [C.c_int32]
-    return _lib
+    """The oracle library in use: liboracle.so, or a mutant build while a
+    test has planted a mistake (plant_mistake)."""
+    if _active not in _libs:
+        if _active == 0:
+            path = build()
+        else:
+            from . import mutants
+            path = mutants.build(_active)
+        _libs[_active] = _declare(C.CDLL(path))
+    return _libs[_active]
 
 
 def _dp(a):
@@ -115,8 +124,18 @@ def kernel_dwdr(r, h, dim):
 
 
 def plant_mistake(which: int):
-    """Switch on a known mistake (0 switches it off) to show a pin catches it."""
-    lib().or_plant_mistake(int(which))
+    """Route the oracle calls that follow (module functions and Sims created
+    from now on) to the mutant build with mistake `which` planted, to show
+    that a pin catches it; 0 returns to the oracle itself.  The mutants are
+    separate builds (oracle/mutants.py): the oracle's own source and library
+    have a single arithmetic path."""
+    global _active
+    which = int(which)
+    if which != 0:
+        from . import mutants
+        if which not in mutants.MUTANTS:
+            raise KeyError(f"no planted mistake {which}")
+    _active = which
 
 
 def make_params(case, **over) -> Params:
@@ -175,7 +194,8 @@ class Sim:
                       ("x", "y", "z", "u", "v", "w", "m", "rho", "p", "wall_u", "wall_v", "wall_w")]
         kind = np.ascontiguousarray(c["kind"], np.int32)
         a = self._keep
-        self.h = lib().or_create(C.byref(self.P), self.n, _dp(a[0]), _dp(a[1]), _dp(a[2]),
+        self._L = lib()
+        self.h = self._L.or_create(C.byref(self.P), self.n, _dp(a[0]), _dp(a[1]), _dp(a[2]),
                                  _dp(a[3]), _dp(a[4]), _dp(a[5]), _dp(a[6]), _dp(a[7]),
                                  _dp(a[8]), _ip(kind), _dp(a[9]), _dp(a[10]), _dp(a[11]))
         if not self.h:
@@ -183,22 +203,22 @@ class Sim:
 
     def __del__(self):
         if getattr(self, "h", None):
-            lib().or_destroy(self.h)
+            self._L.or_destroy(self.h)
             self.h = None
 
     def get(self, field):
         out = np.zeros(self.n)
-        if lib().or_get(self.h, field.encode(), _dp(out)) != 0:
+        if self._L.or_get(self.h, field.encode(), _dp(out)) != 0:
             raise KeyError(field)
         return out
 
     def set(self, field, values):
         arr = np.ascontiguousarray(values, np.float64)
-        if lib().or_set(self.h, field.encode(), _dp(arr)) != 0:
+        if self._L.or_set(self.h, field.encode(), _dp(arr)) != 0:
             raise KeyError(field)
 
     def build_neighbors(self):
-        if lib().or_build_neighbors(self.h) < 0:
+        if self._L.or_build_neighbors(self.h) < 0:
             raise MemoryError("neighbour search failed")
 
     def neighbor_list(self):
@@ -206,35 +226,35 @@ class Sim:
         cap = max(1024, self.n * 64)
         while True:
             idx = np.zeros(cap, np.int32)
-            tot = lib().or_neighbor_list(self.h, _ip(counts), _ip(idx), cap)
+            tot = self._L.or_neighbor_list(self.h, _ip(counts), _ip(idx), cap)
             if tot >= 0:
                 return counts, idx[:tot].copy()
             cap *= 2
 
     def density(self):
-        lib().or_density(self.h)
+        self._L.or_density(self.h)
 
     def wall_normals(self):
-        lib().or_wall_normals(self.h)
+        self._L.or_wall_normals(self.h)
 
     def ghost_velocity(self, slip):
-        lib().or_ghost_velocity(self.h, int(slip))
+        self._L.or_ghost_velocity(self.h, int(slip))
 
     def stage1(self):
-        lib().or_stage1(self.h)
+        self._L.or_stage1(self.h)
 
     def ppe_setup(self):
-        lib().or_ppe_setup(self.h)
+        self._L.or_ppe_setup(self.h)
 
     def ppe_iterate(self):
         d = Diag()
-        lib().or_ppe_iterate(self.h, C.byref(d))
+        self._L.or_ppe_iterate(self.h, C.byref(d))
         return d
 
     def ppe_apply(self, p):
         p = np.ascontiguousarray(p, np.float64)
         out = np.zeros(self.n)
-        lib().or_ppe_apply(self.h, _dp(p), _dp(out))
+        self._L.or_ppe_apply(self.h, _dp(p), _dp(out))
         return out
 
     def ppe_export(self):
@@ -243,34 +263,34 @@ class Sim:
         tot = idx.size
         diag = np.zeros(n); rhs = np.zeros(n); act = np.zeros(n, np.int32)
         fac = np.zeros(max(tot, 1)); ws = np.zeros(n); wh = np.zeros(n); ww = np.zeros(max(tot, 1))
-        lib().or_ppe_export(self.h, _dp(diag), _dp(rhs), _ip(act), _dp(fac), _dp(ws), _dp(wh), _dp(ww))
+        self._L.or_ppe_export(self.h, _dp(diag), _dp(rhs), _ip(act), _dp(fac), _dp(ws), _dp(wh), _dp(ww))
         return dict(counts=counts, idx=idx, diag=diag, rhs=rhs, active=act, fac=fac[:tot],
                     wall_s=ws, wall_h=wh)
 
     def pressure_gradient(self):
-        lib().or_pressure_gradient(self.h)
+        self._L.or_pressure_gradient(self.h)
 
     def gtvf(self):
-        lib().or_gtvf(self.h)
+        self._L.or_gtvf(self.h)
 
     def update(self):
-        lib().or_update(self.h)
+        self._L.or_update(self.h)
 
     def ppe_solve(self, tol, max_iter):
         d = Diag()
-        rc = lib().or_ppe_solve(self.h, float(tol), int(max_iter), C.byref(d))
+        rc = self._L.or_ppe_solve(self.h, float(tol), int(max_iter), C.byref(d))
         return rc, d
 
     def step(self, nsteps=1):
         ds = (Diag * max(1, nsteps))()
-        rc = lib().or_step(self.h, int(nsteps), ds)
+        rc = self._L.or_step(self.h, int(nsteps), ds)
         return rc, [ds[i] for i in range(nsteps)]
 
     @property
     def dt(self):
         """Time step of the next step."""
-        return lib().or_get_dt(self.h)
+        return self._L.or_get_dt(self.h)
 
     @property
     def p_ref(self):
-        return lib().or_get_pref(self.h)
+        return self._L.or_get_pref(self.h)

@@ -30,9 +30,6 @@
 #define FLUID 0
 #define WALL 1
 
-static int g_plant = 0; /* planted-mistake switch for pin-sensitivity tests */
-void or_plant_mistake(int32_t which) { g_plant = which; }
-
 struct or_sim {
   or_params prm;
   int64_t n;
@@ -92,7 +89,7 @@ double or_kernel_w(double r, double h, int32_t dim) {
   double w = 0.0;
   if (q < 3.0) w += p5(3.0 - q);
   if (q < 2.0) w -= 6.0 * p5(2.0 - q);
-  if (q < 1.0 && g_plant != 1) w += 15.0 * p5(1.0 - q);
+  if (q < 1.0) w += 15.0 * p5(1.0 - q);
   return or_sigma(h, dim) * w;
 }
 
@@ -101,7 +98,7 @@ double or_kernel_dwdr(double r, double h, int32_t dim) {
   double dw = 0.0;
   if (q < 3.0) dw -= 5.0 * p4(3.0 - q);
   if (q < 2.0) dw += 30.0 * p4(2.0 - q);
-  if (q < 1.0 && g_plant != 1) dw -= 75.0 * p4(1.0 - q);
+  if (q < 1.0) dw -= 75.0 * p4(1.0 - q);
   return or_sigma(h, dim) * dw / h;
 }
 
@@ -424,7 +421,6 @@ void or_density(or_sim *s) {
     double acc = 0.0;
     for (int64_t t = s->nstart[i]; t < s->nstart[i + 1]; ++t) {
       int64_t j = s->nidx[t];
-      if (g_plant == 13 && s->kind[j] != FLUID) continue;   /* planted: walls left out */
       double dx[3];
       double r2 = or_pair(&s->prm, (const double *const *)s->x, i, j, dx);
       acc += s->m[j] * or_kernel_w(sqrt(r2), s->prm.h, s->prm.dim);
@@ -458,7 +454,7 @@ void or_wall_normals(or_sim *s) {
       for (int k = 0; k < 3; ++k) acc[k] -= vj * g[k];
     }
     double mag = sqrt(or_dot(acc, acc));
-    const int keep = g_plant == 10 ? mag > 0.0 : mag >= 1.0 / (4.0 * h);
+    const int keep = mag >= 1.0 / (4.0 * h);
     for (int k = 0; k < 3; ++k) ns[k][i] = keep ? acc[k] / mag : 0.0;
   }
   for (int64_t i = 0; i < n; ++i) {
@@ -474,7 +470,7 @@ void or_wall_normals(or_sim *s) {
       for (int k = 0; k < 3; ++k) acc[k] += wv * ns[k][j];
     }
     double mag = sqrt(or_dot(acc, acc));
-    if (mag > 1e-6 || (g_plant == 9 && mag > 0.0))
+    if (mag > 1e-6)
       for (int k = 0; k < 3; ++k) s->nrm[k][i] = acc[k] / mag;
   }
   for (int k = 0; k < 3; ++k) free(ns[k]);
@@ -567,26 +563,20 @@ void or_stage1(or_sim *s) {
       double uij[3] = {ui[0] - uj[0], ui[1] - uj[1], ui[2] - uj[2]};
       double rdw = or_dot(dx, g);
       double visc = mj * 4.0 * P->nu / (ri + rj) * rdw / (r2 + eh2);
-      if (g_plant == 4) visc *= 0.5;
       for (int k = 0; k < 3; ++k) fi[k] += visc * uij[k];
       if (P->alpha > 0.0) {
         double vr = or_dot(uij, dx);
-        if (vr < 0.0 || g_plant == 7) {
+        if (vr < 0.0) {
           double phi = vr / (r2 + eh2);
           double pi_ij = -P->alpha * h * P->c0 * phi / (0.5 * (ri + rj));
-          for (int k = 0; k < 3; ++k) fi[k] -= ((g_plant == 8) ? -1.0 : 1.0) * mj * pi_ij * g[k];
+          for (int k = 0; k < 3; ++k) fi[k] -= mj * pi_ij * g[k];
         }
       }
       if (s->kind[j] == FLUID) {
         double dti[3] = {s->ut[0][i] - ui[0], s->ut[1][i] - ui[1], s->ut[2][i] - ui[2]};
         double dtj[3] = {s->ut[0][j] - uj[0], s->ut[1][j] - uj[1], s->ut[2][j] - uj[2]};
-        if (g_plant == 11) {            /* planted: the tensor transposed */
-          double ai = or_dot(ui, g) / ri, aj = or_dot(uj, g) / rj;
-          for (int k = 0; k < 3; ++k) fi[k] += mj * (dti[k] * ai + dtj[k] * aj);
-        } else {
-          double ai = or_dot(dti, g) / ri, aj = (g_plant == 12) ? 0.0 : or_dot(dtj, g) / rj;
-          for (int k = 0; k < 3; ++k) fi[k] += mj * (ui[k] * ai + uj[k] * aj);
-        }
+        double ai = or_dot(dti, g) / ri, aj = or_dot(dtj, g) / rj;
+        for (int k = 0; k < 3; ++k) fi[k] += mj * (ui[k] * ai + uj[k] * aj);
       }
     }
     for (int k = 0; k < 3; ++k) {
@@ -636,15 +626,14 @@ void or_ppe_setup(or_sim *s) {
         double rj = s->rho[j], mj = s->m[j];
         double uij[3];
         for (int k = 0; k < 3; ++k) uij[k] = s->u[k][i] - or_vel(s, j, k);
-        double sgn = (g_plant == 2) ? 1.0 : -1.0;
-        rhs += sgn * mj / (rj * P->dt) * or_dot(uij, g);
+        rhs += -mj / (rj * P->dt) * or_dot(uij, g);
         double fac = 4.0 * mj / (ri * (ri + rj)) * or_dot(dx, g) / (r2 + eh2);
         s->fac[t] = fac;
         dg += fac;
       }
       s->rhs[i] = rhs;
       s->diag[i] = dg;
-      int fs = P->free_surface && (ri / P->rho0 < P->fs_ratio) && g_plant != 14;
+      int fs = P->free_surface && (ri / P->rho0 < P->fs_ratio);
       s->active[i] = (dg != 0.0) && !fs;
       if (!s->active[i]) s->p[i] = 0.0;
       else {
@@ -662,8 +651,7 @@ void or_ppe_setup(or_sim *s) {
         double wv = or_kernel_w(sqrt(r2), h, P->dim);
         s->fac[t] = wv;
         sw += wv;
-        double sg = (g_plant == 3) ? -1.0 : 1.0;
-        for (int k = 0; k < 3; ++k) acc[k] += s->rho[j] * sg * dx[k] * wv;
+        for (int k = 0; k < 3; ++k) acc[k] += s->rho[j] * dx[k] * wv;
       }
       double gv[3] = {P->g[0], P->g[1], P->dim == 3 ? P->g[2] : 0.0};
       s->ws[i] = sw;
@@ -930,7 +918,7 @@ void or_pressure_gradient(or_sim *s) {
       double rj = s->rho[j], pj = s->p[j], mj = s->m[j];
       double c;
       if (P->pgrad_symm) c = -mj * (pi / (ri * ri) + pj / (rj * rj));
-      else c = -mj / (ri * rj) * ((g_plant == 6) ? (pi - pj) : (pj - pi));
+      else c = -mj / (ri * rj) * (pj - pi);
       for (int k = 0; k < 3; ++k) fi[k] += c * g[k];
     }
     // total acceleration of this step, f_p + (f_visc + f_avisc + f_astress
@@ -1080,7 +1068,7 @@ int32_t or_step(or_sim *s, int32_t nsteps, or_diag *d) {
     memset(&dd, 0, sizeof(dd));
     if (s->prm.ppe_solver == 1) or_ppe_bicgstab(s, &dd);
     else or_ppe_iterate(s, &dd);
-    if (!s->pref_set || g_plant == 15) {   /* planted 15: p_ref re-taken every step */
+    if (!s->pref_set) {
       double mx = 0.0;
       int first = 1;
       for (int64_t i = 0; i < s->n; ++i)

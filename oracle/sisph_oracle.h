@@ -103,8 +103,6 @@ int32_t or_ppe_solve(or_sim *s, double tol, int32_t max_iter, or_diag *d);
 double or_get_pref(const or_sim *s);
 /* Time step of the next step (changes with the adaptive rule). */
 double or_get_dt(const or_sim *s);
-/* Test hook: plant a known mistake (0 = none) so a test can show a pin fails. */
-void or_plant_mistake(int32_t which);
 
 #ifdef __cplusplus
 }
