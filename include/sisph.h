@@ -296,15 +296,19 @@ const char *sisph_version(void);
  * library is loaded; every GPU that loads the library holds it until the
  * process exits.  Limits: n <= SISPH_NOALLOC_MAX_POINTS points and a cell
  * grid (cells of side >= 3h over [lo, hi)) of at most SISPH_NOALLOC_MAX_CELLS
- * cells; larger inputs are rejected with SISPH_EINVAL and a message.  A row
- * with more than cap neighbours returns SISPH_ECAPACITY (its count is
- * clipped to cap).  The first call on each device looks up the device address
- * of the scratch array with that device current; make that first call before
- * any stream capture begins.  Every call shares the array and it keeps the
- * last call's contents (each call clears what must start at zero); calls
- * whose kernels overlap on the GPU race on it, so serialise them.  The
- * library calls no cudaMalloc, cudaFree or allocating routine here.  Errors
- * are reported through sisph_last_error(NULL). */
+ * cells; larger inputs are rejected with SISPH_EINVAL and a message.  Points
+ * outside [lo, hi) in a non-periodic direction are searched from the edge
+ * cell they are clamped into, so their rows are still exact.  A row with more
+ * than cap neighbours makes the call return SISPH_ECAPACITY; its count is
+ * clipped to cap and the row holds the cap smallest indices of N(i), in
+ * ascending order.  Each call looks up the device address of the scratch
+ * array on the current device (no allocation).  The call reads a status word
+ * back and waits for its kernels, so a `stream` that is capturing a graph is
+ * rejected with SISPH_EINVAL before anything is launched.  Every call shares
+ * the array and it keeps the last call's contents (each call clears what
+ * must start at zero); calls whose kernels overlap on the GPU race on it, so
+ * serialise them.  The library calls no cudaMalloc, cudaFree or allocating
+ * routine here.  Errors are reported through sisph_last_error(NULL). */
 #define SISPH_NOALLOC_MAX_POINTS 65536
 #define SISPH_NOALLOC_MAX_CELLS 65536
 int sisph_neighbors_noalloc(int32_t dim, int32_t n, const double *x_dev, const double *y_dev,

@@ -14,10 +14,13 @@
 // Every call shares that array and it keeps the last call's contents; each
 // call clears what must start at zero.  Calls whose kernels overlap on the GPU
 // (for example on two streams at once) race on the array: serialise them.
+// In host code the array's name is only a host-side stand-in: every call
+// looks up the array's device address on the current device (the lookup
+// allocates nothing), so a pointer from an earlier context -- before a
+// cudaDeviceReset, or on another context of the same device -- is never used.
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 #include <string>
 
 #include "sisph_internal.h"
@@ -39,10 +42,6 @@ constexpr int kOffStatus = kOffPerm + kNaMaxPoints;        // overflow flag
 constexpr int kScratchWords = kOffStatus + 64;
 
 static __device__ __align__(256) unsigned int g_na_scratch[kScratchWords];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_na_mutex;
-void *g_na_ptr[kMaxDevices] = {nullptr};
 
 struct NaGrid {
   int dim, n, ncell, cap;
@@ -140,7 +139,9 @@ __global__ void k_na_cellsort(int ncell, unsigned int *scr) {
 
 // Row i (the caller's order): every j with |r_ij|^2 < (3h)^2, minimum image,
 // |r_ij|^2 = dx*dx + dy*dy (+ dz*dz) unfused, ascending j; rows are
-// row-major, cap entries each.
+// row-major, cap entries each.  A row with more than cap neighbours keeps its
+// cap smallest indices (a larger index is dropped, a smaller one displaces
+// the row's largest) and raises the status word.
 __global__ void k_na_rows(NaGrid G, const double *x0, const double *x1, const double *x2,
                           unsigned int *scr, int *counts, int *idx) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -185,16 +186,15 @@ __global__ void k_na_rows(NaGrid G, const double *x0, const double *x1, const do
           r2 = __dadd_rn(r2, __dmul_rn(d[1], d[1]));
           if (G.dim == 3) r2 = __dadd_rn(r2, __dmul_rn(d[2], d[2]));
           if (r2 < G.cut2) {
-            if (cnt < G.cap) {
-              // insert in ascending order
-              int b = cnt;
+            if (cnt >= G.cap) atomicOr(&scr[kOffStatus], 1u);
+            if (cnt < G.cap || j < row[G.cap - 1]) {
+              // insert in ascending order (a full row drops its largest)
+              int b = cnt < G.cap ? cnt : G.cap - 1;
               while (b > 0 && row[b - 1] > j) {
                 row[b] = row[b - 1];
                 --b;
               }
               row[b] = j;
-            } else {
-              atomicOr(&scr[kOffStatus], 1u);
             }
             ++cnt;
           }
@@ -220,6 +220,19 @@ extern "C" int sisph_neighbors_noalloc(int32_t dim, int32_t n, const double *x_d
   if (!x_dev || !y_dev || (dim == 3 && !z_dev) || !counts_dev || !idx_dev || !lo || !hi || !periodic)
     return na_fail(SISPH_EINVAL, "noalloc: a required pointer is NULL");
   if (!(h > 0.0) || cap < 1) return na_fail(SISPH_EINVAL, "noalloc: h > 0 and cap >= 1 required");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  {
+    // the call reads a status word back and waits for its kernels, which a
+    // capturing stream does not allow: reject it before anything is launched
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t ec = cudaStreamIsCapturing(st, &cs);
+    if (ec != cudaSuccess) {
+      cudaGetLastError();
+      return na_fail(SISPH_ECUDA, std::string("noalloc: ") + cudaGetErrorString(ec));
+    }
+    if (cs != cudaStreamCaptureStatusNone)
+      return na_fail(SISPH_EINVAL, "noalloc: the stream is capturing a graph; the call synchronises it");
+  }
   NaGrid G{};
   G.dim = dim;
   G.n = n;
@@ -249,27 +262,16 @@ extern "C" int sisph_neighbors_noalloc(int32_t dim, int32_t n, const double *x_d
                                      std::to_string(kNaMaxCells));
   G.ncell = int(ncell);
 
-  // set-up, once per device, with that device current: the device address of
-  // the scratch array (its name in host code is only a host-side stand-in)
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return na_fail(SISPH_ECUDA, std::string("noalloc: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return na_fail(SISPH_EINVAL, "noalloc: device index too large");
+  // the device address of the scratch array on the current device (the
+  // array's name in host code is only a host-side stand-in), looked up at
+  // every call with that device current
   void *ptr = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[dev]) {
-      e = cudaGetSymbolAddress(&g_na_ptr[dev], g_na_scratch);
-      if (e != cudaSuccess) {
-        g_na_ptr[dev] = nullptr;
-        cudaGetLastError();
-        return na_fail(SISPH_ECUDA, std::string("noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      }
-    }
-    ptr = g_na_ptr[dev];
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_na_scratch);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return na_fail(SISPH_ECUDA, std::string("noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
   }
   unsigned int *scr = static_cast<unsigned int *>(ptr);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int T = 256;
   const double *z = dim == 3 ? z_dev : x_dev;
   k_na_clear<<<(G.ncell + 1 + T - 1) / T + 1, T, 0, st>>>(scr, G.ncell);
