@@ -30,6 +30,7 @@ for name, make in (("tgv", lambda: workloads.taylor_green(24, perturb=0.05, seed
         sim.build_neighbors()
         for f in ("x", "y", "u", "v", "p"):
             out[f"{{name}}_{{prec}}_{{f}}"] = sim.get(f)
+        out[f"{{name}}_{{prec}}_fluid"] = (make()["kind"] == 0)
         out[f"{{name}}_{{prec}}_pairs"] = np.array([np.sum(sim.neighbors()[0])])
         sim.close()
 np.savez({path!r}, **out)
@@ -53,12 +54,22 @@ def test_checked_build_matches_the_normal_build(tmp_path):
     b = _run(tmp_path / "checked.npz", True)
     assert sorted(a.files) == sorted(b.files)
     for k in a.files:
+        if k.endswith("_fluid"):
+            continue
         if k.endswith("_pairs"):
             # neighbour totals: positions agree to rounding, lattice ties may flip
             assert abs(int(a[k][0]) - int(b[k][0])) <= 0.001 * int(a[k][0]), k
             continue
         if "_1_" in k and k[-1] in "uvp":
-            continue   # MIXED walls with fluid only at exactly 3h: p and ghost u flip
+            # MIXED pressure and velocity: a wall whose only fluid neighbours
+            # sit at exactly 3h may flip between W = 0 and a rounding-sized
+            # weight, which changes its own p and ghost u but no fluid row;
+            # the fluid rows agree within the stated FP32 bound (1e-4
+            # relative L2)
+            fl = a[k[:-1] + "fluid"]
+            x, y = a[k][fl], b[k][fl]
+            assert np.linalg.norm(x - y) / max(np.linalg.norm(x), 1e-300) < 1e-4, k
+            continue
         tol = 1e-12 if "_0_" in k else 1e-5
         scale = max(np.max(np.abs(a[k])), 1e-300)
         assert np.max(np.abs(a[k] - b[k])) / scale < tol, k

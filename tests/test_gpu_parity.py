@@ -149,9 +149,10 @@ def _resync(ref, sim, case):
 
 
 def test_tgv_lattice_steps_fp64_resynced(sisph):
-    # The unperturbed 50 x 50 lattice at p_ref = 100 amplifies any rounding
-    # difference about tenfold per step (the GTVF update is above its
-    # stability limit there), so each step is checked from a common state.
+    # On the unperturbed 50 x 50 lattice the sweeps at tol = 0 leave the
+    # periodic PPE's mean pressure drifting, and every step starts from the
+    # oracle's state again so that a rounding difference in one step is not
+    # carried into the next: each step is checked from a common state.
     case = with_params(workloads.taylor_green(50), tol=0.0, max_iter=20)
     sim = sisph.Simulation(case)
     ref = oracle.Sim(case)
