@@ -259,11 +259,13 @@ class ClockSampler:
 
 def sweep_bytes(counts_fluid, n_walls_rows, wall_counts, prec_bytes):
     """Algorithmic bytes of one damped-Jacobi sweep of the stored-coefficient
-    form: per fluid neighbour slot an index and a coefficient; per fluid
-    particle the source, omega/D, the slot count, p^k read and p^{k+1}
-    written; per wall Shepard entry an index and a weight, per wall its count,
-    1/S, H and p_w written.  Neighbour pressures are gathers that the Morton
-    order keeps in cache, so they are not counted."""
+    form: per fluid neighbour slot an index and a coefficient (counts_fluid:
+    the slots of each fluid row -- N(i) without i itself in MIXED, whose
+    packed slots leave out the zero coefficient fac_ii); per fluid particle
+    the source, omega/D, the slot count, p^k read and p^{k+1} written; per
+    wall Shepard entry an index and a weight, per wall its count, 1/S, H and
+    p_w written.  Neighbour pressures are gathers that the Morton order keeps
+    in cache, so they are not counted."""
     rb = prec_bytes
     fluid = np.sum(counts_fluid) * (4 + rb) + counts_fluid.size * (3 * rb + 4 + rb)
     walls = np.sum(wall_counts) * (4 + rb) + n_walls_rows * (4 + 3 * rb)
@@ -498,7 +500,8 @@ def run_ours(args, rank, world):
         walls = np.nonzero(~flc)[0] + offs[ci]
         wall_counts = np.array([np.sum(fl[idx[starts[w]:starts[w + 1]]]) for w in walls]) \
             if walls.size else np.zeros(0)
-        fb, wb = sweep_bytes(streamed[sl][flc], walls.size, wall_counts, rb)
+        slots = streamed[sl][flc] - (1 if mixed else 0)     # MIXED slots skip i itself
+        fb, wb = sweep_bytes(slots, walls.size, wall_counts, rb)
         its = float(it1[ci] - it0[ci])
         sweep_total += its * fb + (its + args.steps) * wb
         pairs += its * float(np.sum(cnt_c[flc]))
@@ -678,43 +681,62 @@ def p_l1_tgv(sim, case, t, re=100.0):
 
 
 def study_tolerance(args):
-    """The paper's tolerance study (Sec. 3.1, Table 1; Sec. 4.1): PPE sweeps per
-    step, accuracy and throughput against epsilon, one JSON line per run."""
+    """The paper's tolerance study (Sec. 3.1, Table 1; Sec. 4.1): for each
+    epsilon, PPE sweeps per step, the device time per step, particle-steps/s
+    and PPE interactions/s, and the accuracy -- p_L1 (Eq. tgv_p_l1) and the
+    decay rate of the Taylor-Green vortex (the benchmark's perturbed 400 x 400
+    case), the final residual elsewhere -- one JSON line per run.  Every run
+    starts at t = 0 and replays `steps` steps from a CUDA graph, L2 flushed
+    between steps."""
     import torch
     from paper_1908_01762_gb300 import sisph
     import paper_1908_01762_gb300 as pkg
     pkg.build()
-    # the benchmark's 400 x 400 TGV, a 100 x 100 cavity and the 2D dam break
     problems = {
-        "tgv400_re100": lambda tol: workloads.taylor_green(400, perturb=0.05, tol=tol),
+        "tgv400_perturbed_re100": lambda tol: workloads.taylor_green(400, perturb=0.05, seed=1908,
+                                                                      tol=tol),
         "cavity100_re100": lambda tol: workloads.lid_driven_cavity(100, tol=tol),
         "dam_break_2d_dx0.01": lambda tol: workloads.dam_break_2d(dx=0.01, tol=tol),
     }
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     for name, make in problems.items():
-        for tol in (0.1, 0.05, 1e-2, 5e-3, 1e-3, 5e-4):
+        for tol in (0.1, 0.05, 1e-2, 5e-3, 1e-3, 5e-4, 1e-4):
             case = make(tol)
             sim = sisph.Simulation(case, precision=sisph.MIXED, use_graph=1)
-            t0 = time.perf_counter()
+            sisph.sisph_set_stream(sim.h, stream.cuda_stream)
+            fl = case["kind"] == 0
+            ms, pairs = 0.0, 0.0
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             try:
                 for _ in range(args.steps):
+                    it0 = sim.stats()[0].total_iters
+                    flush.fill_(1.0)
+                    e0.record(stream)
                     sim.step(1)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms += e0.elapsed_time(e1)
+                    cnt = sim.get("ncount")
+                    pairs += float(sim.stats()[0].total_iters - it0) * float(np.sum(cnt[fl]))
             except sisph.SisphError as err:
                 print(json.dumps({"study": "tolerance", "problem": name, "tol": tol,
                                   "failed": str(err)}), flush=True)
                 sim.close()
                 continue
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
             st = sim.stats()[0]
             out = {"study": "tolerance", "problem": name, "tol": tol, "steps": args.steps,
-                   "sweeps_per_step": st.total_iters / st.solves,
-                   "particle_steps_per_s": case["n"] * args.steps / dt}
+                   "n": case["n"], "sweeps_per_step": st.total_iters / st.solves,
+                   "ms_per_step": ms / args.steps,
+                   "particle_steps_per_s": case["n"] * args.steps / (ms * 1e-3),
+                   "ppe_interactions_per_s": pairs / (ms * 1e-3),
+                   "final_residual": st.residual}
             if name.startswith("tgv"):
                 t = args.steps * case["params"]["dt"]
                 out["p_l1"] = p_l1_tgv(sim, case, t) / case["n"]
                 e = np.sum(case["m"] * (sim.get("u") ** 2 + sim.get("v") ** 2))
-                e0 = np.sum(case["m"] * (case["u"] ** 2 + case["v"] ** 2))
-                out["decay_rate"] = math.log(e / e0) / (2 * t)
+                en0 = np.sum(case["m"] * (case["u"] ** 2 + case["v"] ** 2))
+                out["decay_rate"] = math.log(e / en0) / (2 * t)
                 out["decay_rate_exact"] = -8 * math.pi ** 2 / 100.0
             print(json.dumps(out), flush=True)
             sim.close()

@@ -268,7 +268,7 @@ cudaError_t capture_rebuild_conditional(sisph_t s, int mode, bool first) {
 // the device: in a captured step by a conditional node (unless a profiled
 // site lies in the group, whose kernels then return at once without a
 // rebuild), in direct launches by reading the decision back.
-cudaError_t do_refresh(sisph_t s, int mode, bool first, bool exact = false) {
+cudaError_t do_refresh(sisph_t s, int mode, bool first, bool exact = false, bool density = false) {
   Launch L = mk_launch(s);
   cudaError_t e = launch_refresh_check(s->S, L, mode);
   if (e != cudaSuccess) return e;
@@ -284,7 +284,7 @@ cudaError_t do_refresh(sisph_t s, int mode, bool first, bool exact = false) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e == cudaSuccess && any) e = launch_refresh_rebuild(s->S, L, mode, first, false);
   }
-  if (e == cudaSuccess) e = launch_refresh_finish(s->S, L, mode, exact);
+  if (e == cudaSuccess) e = launch_refresh_finish(s->S, L, mode, exact, density);
   return e;
 }
 
@@ -308,9 +308,10 @@ cudaError_t do_ppe(sisph_t s) {
 
 cudaError_t do_step(sisph_t s) {
   Launch L = mk_launch(s);
-  cudaError_t e = do_refresh(s, 0, false);            // neighbours at r^n
+  // neighbours at r^n; in MIXED the same pass sums rho (Eq. summation_density)
+  cudaError_t e = do_refresh(s, 0, false, false, s->S.mixed != 0);
   if (e == cudaSuccess && s->adaptive) e = launch_speed_max(s->S, L, 0);  // max|u^n| (Sec. 3.2)
-  if (e == cudaSuccess) e = launch_density(s->S, L);  // rho (Eq. summation_density)
+  if (e == cudaSuccess && !s->S.mixed) e = launch_density(s->S, L);  // rho (Eq. summation_density)
   if (e == cudaSuccess) e = launch_ghost(s->S, L, 0); // no-slip ghost velocity
   if (e == cudaSuccess) e = launch_stage1(s->S, L);   // u*, r* (Eqs. int:vint, int:rnp1)
   if (e == cudaSuccess) e = do_refresh(s, 1, false);  // neighbours at r*
@@ -720,6 +721,7 @@ int sisph_batch_create(int32_t ncases, const sisph_particles *parts, const sisph
     e = dalloc(s, &q, ell_size(S.cap, (long long)N) * 8);
     S.coef = q;
   }
+  A(&S.pcnt, N);
   AR(&S.prhs, N);
   AR(&S.pwd, N);
   for (int q = 0; q < 4; ++q) AR(&S.pb[q], N);

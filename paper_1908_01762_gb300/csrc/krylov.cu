@@ -91,7 +91,7 @@ __device__ __forceinline__ R apply_row(const State &S, const CaseDev &P, int i, 
   const R yi = b ? a[i] - al * b[i] : a[i];
   if (!active) return yi;
   const long long sb = slot_base(S, i);
-  const int cnt = S.ncnt[i];
+  const int cnt = S.pcnt[i];
   const int fend = P.fbeg + P.nf;
   R acc = R(S.diag_out[i]) * yi;
   double bw = 0.0;

@@ -420,6 +420,8 @@ __global__ void __launch_bounds__(256) k_skin(State S) {
   int cnt = 0;
   bool over = false;
   auto append = [&](unsigned entry) {
+    // a fluid row's own entry is placed first, before the scan (below)
+    if (!wall_row && (entry & kIdxMask) == unsigned(i)) return;
     if (cnt < S.scap) S.snbr[ell_at(S.scap, cnt, i)] = entry;
     else over = true;
     ++cnt;
@@ -503,6 +505,10 @@ __global__ void __launch_bounds__(256) k_skin(State S) {
     head = cnt;
     scan(0, 0, false);
   } else {
+    // a fluid row starts with i itself, so that its lists (and the MIXED PPE
+    // slots, which leave i out) keep one layout across the warp's rows
+    S.snbr[ell_at(S.scap, 0, i)] = unsigned(i) | (stencil_code(0, 0, 0) << kCodeShift);
+    cnt = 1;
     scan(0, 1, false);
   }
   if (over) {
@@ -577,7 +583,11 @@ struct PeriodicBox {
   double half[3], L[3];
 };
 
-template <int DIM, bool EXACT>
+// DENS (MIXED, in-step refresh at r^n): a fluid row also sums its summation
+// density (Eq. summation_density) over the pairs it keeps, in the order they
+// are kept, with the same FP32 pair vector as the density pass, so the step
+// needs no separate density pass over N(i).
+template <int DIM, bool EXACT, bool DENS = false>
 __global__ void __launch_bounds__(256, 4) k_filter(State S) {
   constexpr int kBand = DIM == 3 ? 48 : 16;   // at most 64 (one bit each below)
   constexpr int kU = DIM == 3 ? 4 : 8;         // candidates whose loads go out together
@@ -604,6 +614,14 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
     if (cnt < S.cap) S.nbr[ell_at(S.cap, cnt, i)] = entry;
     else over = true;
     ++cnt;
+  };
+  const bool dens = DENS && blockIdx.x < unsigned(S.nft);
+  const float dih = float(P.inv_h);
+  float rho = 0.f;
+  // a kept pair of a fluid row: its list entry and, with DENS, m_j W_ij
+  auto keep = [&](unsigned entry, float r2f, float mj) {
+    append(entry);
+    if (DENS && dens) rho += mj * poly_w<float>(sqrtf(r2f) * dih);
   };
   auto exact = [&](unsigned entry) {
     const double xi[3] = {S.x[0][i], S.x[1][i], DIM == 3 ? S.x[2][i] : 0.0};
@@ -644,10 +662,10 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
       const float r2f = pair_f<DIM>(lc, pi, pj[u], e[u] >> kCodeShift, d);
       const bool near = own_near && near_cell<DIM>(pj[u], lc);
       if (near && r2f < lo_band) {
-        append(e[u]);
+        keep(e[u], r2f, pj[u].w);
       } else if (!near) {
         if (ex && nband < kBand) band[nband++] = e[u];
-        else if (exact(e[u])) append(e[u]);
+        else if (exact(e[u])) keep(e[u], r2f, pj[u].w);
       } else if (ex && r2f <= hi_band) {
         if (nband < kBand) band[nband++] = e[u];
         else if (exact(e[u])) append(e[u]);     // a full band: decided here
@@ -677,6 +695,11 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
     cnt = S.cap;
   }
   S.ncnt[i] = cnt;
+  if (DENS && dens) {
+    rho *= float(P.sig_h);
+    S.rho[i] = double(rho);
+    S.vf4[i].w = rho;
+  }
 }
 
 // The rebuild group of a captured step sits in a conditional graph node whose
@@ -741,7 +764,7 @@ cudaError_t launch_refresh_rebuild(const State &S, const Launch &L, int mode, bo
   return cudaGetLastError();
 }
 
-cudaError_t launch_refresh_finish(const State &S, const Launch &L, int mode, bool exact) {
+cudaError_t launch_refresh_finish(const State &S, const Launch &L, int mode, bool exact, bool density) {
   const int nt = S.nft + S.nwt;
   const int nb = (S.n + 255) / 256;
   if (L.before) L.before(L.ctx, "sync");
@@ -752,6 +775,9 @@ cudaError_t launch_refresh_finish(const State &S, const Launch &L, int mode, boo
   if (exact) {
     if (S.dim == 2) k_filter<2, true><<<nt, S.T, 0, L.stream>>>(S);
     else k_filter<3, true><<<nt, S.T, 0, L.stream>>>(S);
+  } else if (density && S.mixed) {
+    if (S.dim == 2) k_filter<2, false, true><<<nt, S.T, 0, L.stream>>>(S);
+    else k_filter<3, false, true><<<nt, S.T, 0, L.stream>>>(S);
   } else {
     if (S.dim == 2) k_filter<2, false><<<nt, S.T, 0, L.stream>>>(S);
     else k_filter<3, false><<<nt, S.T, 0, L.stream>>>(S);

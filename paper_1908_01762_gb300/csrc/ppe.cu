@@ -76,7 +76,7 @@ struct DepSet {
 // inactive: p = 0 for the whole solve.  Lambda = max |RHS_i/D_ii| per tile.
 // ---------------------------------------------------------------------------
 template <int DIM, bool MX>
-__global__ void k_setup_fluid(State S) {
+__global__ void __launch_bounds__(256, MX ? 4 : 2) k_setup_fluid(State S) {
   using R = typename std::conditional<MX, float, double>::type;
   const Tile &t = S.ftiles[blockIdx.x];
   int i = t.beg + threadIdx.x;
@@ -106,6 +106,10 @@ __global__ void k_setup_fluid(State S) {
     const R idt = R(1.0 / P.dt);
     const R four_iri = R(4) / ri;
     R rhs = R(0), rc = R(0), dg = R(0), dc = R(0);
+    // MIXED rows whose list starts with i itself (every list a step builds)
+    // leave its zero coefficient out of the packed slots: entry k goes to
+    // slot k - 1; other rows keep one slot per entry
+    const int shift = (MX && (S.nbr[ell_at(S.cap, 0, i)] & kIdxMask) == unsigned(i)) ? 1 : 0;
     ROW_CHUNKS(S, i, {
       const int k = _q0 + _u;
       int j = int(e & kIdxMask);
@@ -141,14 +145,16 @@ __global__ void k_setup_fluid(State S) {
           dg += fac;
         }
       }
+      if (valid && k >= shift)
+        store_coef<R>(S.coef, slot_at(S, k - shift, i), j, fac);
       if (valid) {
-        store_coef<R>(S.coef, slot_at(S, k, i), j, fac);
         if (S.p2p && j != i) {
           const int dt = S.tile_of[j];
           if (dt != int(blockIdx.x)) deps.insert(dt);
         }
       }
     })
+    S.pcnt[i] = S.ncnt[i] - shift;
     bool fs = P.free_surface && (double(ri) / P.rho0 < S.fs_ratio);
     bool active = (dg != R(0)) && !fs;
     static_cast<R *>(S.prhs)[i] = active ? rhs : R(0);
@@ -491,7 +497,7 @@ __global__ void __launch_bounds__(256, sweep_blocks_per_sm(MX, CH)) k_sweeps(Sta
       R dnr = R(0), dpr = R(0);
       if (i < t.end) {
         R acc = prhs[i];
-        const int cnt = S.ncnt[i];
+        const int cnt = S.pcnt[i];
         const long long sb = slot_base(S, i);
         for (int q0 = 0; q0 < cnt; q0 += CH) {
           int jj[CH];
@@ -787,7 +793,7 @@ __global__ void __launch_bounds__(256, MX ? 5 : 4) k_sweeps_p2p(State S) {
       const int i = t.beg + threadIdx.x;
       R dnr = R(0), dpr = R(0);
       if (i < t.end) {
-        R acc = jacobi_sum<R>(S, pc, i, prhs[i], S.ncnt[i]);
+        R acc = jacobi_sum<R>(S, pc, i, prhs[i], S.pcnt[i]);
         R po = pc[i];
         R pnew = pwd[i] * acc + om1 * po;
         pn[i] = pnew;

@@ -164,6 +164,7 @@ struct State {
   long long *nbody;        // rebuild groups run inside conditional graph nodes
   // PPE
   void *coef;              // fac_ij per ELL slot: FP64, or {j, FP32 fac} (MIXED)
+  int *pcnt;               // PPE slots per fluid row: N(i) (FP64), N(i) without i (MIXED)
   void *prhs;              // RHS_i (active) else 0
   void *pwd;               // omega / D_ii (active) else 0
   void *pb[4];             // pressure buffers: p^k in pb[k % 2] (grid barrier
@@ -374,7 +375,10 @@ struct Launch {
 cudaError_t launch_refresh_check(const State &S, const Launch &L, int mode);
 cudaError_t launch_refresh_rebuild(const State &S, const Launch &L, int mode, bool gather_static,
                                    bool count_on_device);
-cudaError_t launch_refresh_finish(const State &S, const Launch &L, int mode, bool exact);
+// density: in MIXED the in-step filter also sums the fluid rows' summation
+// density (the step's refresh at r^n), replacing launch_density there
+cudaError_t launch_refresh_finish(const State &S, const Launch &L, int mode, bool exact,
+                                  bool density = false);
 cudaError_t launch_set_conditional(const State &S, const Launch &L, cudaGraphConditionalHandle h);
 constexpr int kRebuildKernels = 10;   // kernels of launch_refresh_rebuild
 // passes.cu

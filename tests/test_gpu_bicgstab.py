@@ -1,6 +1,8 @@
 """BiCGStab PPE (the Krylov alternative of Sec. 3.1) on the GPU against the
-oracle's BiCGStab: FP64 to 1e-9 relative with the iteration count fixed
-(tol = 0), MIXED within the stated bound after natural convergence; the
+oracle's BiCGStab: FP64 to 1e-10 relative with the iteration count fixed
+(tol = 0) and after natural convergence (measured: 1e-15 to 1e-13), MIXED
+within the stated 1e-4 relative L2 after convergence to 1e-6 (measured
+1e-6); the
 per-case choice inside a batch (a member equals its solo run bit for bit),
 the Jacobi sweeps for singular systems, and fewer iterations than Jacobi at
 the same tolerance."""
@@ -48,7 +50,7 @@ def test_bicgstab_solve_fp64_fixed_iterations(sisph, iters):
     ref.density()
     rc2, d = ref.ppe_solve(0.0, iters)
     assert it[0] == d.iters == iters
-    assert relerr(sim.get("p"), ref.get("p")) < 1e-9
+    assert relerr(sim.get("p"), ref.get("p")) < 1e-10
     sim.close()
 
 
@@ -62,7 +64,7 @@ def test_bicgstab_solve_fp64_converged(sisph):
     rc2, d = ref.ppe_solve(1e-10, 500)
     assert rc == 0 and d.converged
     assert abs(int(it[0]) - d.iters) <= 1
-    assert relerr(sim.get("p"), ref.get("p")) < 1e-8
+    assert relerr(sim.get("p"), ref.get("p")) < 1e-10
     sim.close()
 
 
@@ -78,13 +80,16 @@ def test_bicgstab_steps_fp64(sisph):
         g, o = sim.get(f), ref.get(f)
         if f in ("u", "v"):
             g, o = g[fl], o[fl]
-        assert relerr(g, o) < 1e-9, f
+        assert relerr(g, o) < 1e-10, f
     sim.close()
 
 
 def test_bicgstab_mixed_bound(sisph):
     """MIXED (FP32 vectors, FP64 dot products) against the FP64 oracle, both
-    converged to 1e-6: relative L2 of the fluid pressure within 1e-3.  (The
+    converged to 1e-6: relative L2 of the fluid pressure within the stated
+    1e-4 (measured 1e-6).  At a loose tolerance (1e-4) the two stop a few
+    iterations apart on different paths and differ by about 1e-3, each within
+    its own truncation error of the exact solution.  (The
     outer wall layer of this lattice touches the fluid only at exactly 3h,
     where the FP32 kernel weight is 0: such walls get p = 0; they carry no
     weight in any fluid row, so the fluid is unaffected.)"""
@@ -99,7 +104,7 @@ def test_bicgstab_mixed_bound(sisph):
     g, o = sim.get("p")[fl], ref.get("p")[fl]
     l2 = np.linalg.norm(g - o) / np.linalg.norm(o)
     print("MIXED BiCGStab relative L2", l2)
-    assert l2 < 1e-3
+    assert l2 < 1e-4
     sim.close()
 
 

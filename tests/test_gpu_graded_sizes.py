@@ -11,7 +11,8 @@ FP64: 1e-10 relative on every field after one step with the sweep count
 forced equal on both sides (tol = 0, max_iter = K).  MIXED: the pressure of
 the fluid rows within 1e-4 relative L2 at the same sweep count (periodic
 members with the mean removed: the periodic PPE fixes p up to a constant),
-velocities within 1e-4 relative L2, positions within 1e-5 h; at the natural
+velocities within 1e-4 relative L2, the density within 1e-5, positions
+within 1e-5 h; at the natural
 tolerance the sweep counts agree to within one.  The oracle takes about 10 s
 per step of the 3D dam break on one core.
 """
@@ -76,6 +77,8 @@ def check_mixed(a, b, fl, dim, h, periodic=False):
     assert l2(pa, pb) < 1e-4, ("p", l2(pa, pb))
     for f in ("u", "v", "w")[:dim]:
         assert l2(a[f][fl], b[f][fl]) < 1e-4, (f, l2(a[f][fl], b[f][fl]))
+    # the step's summation density (FP32 sums of FP32 weights)
+    assert l2(a["rho"][fl], b["rho"][fl]) < 1e-5, ("rho", l2(a["rho"][fl], b["rho"][fl]))
     for f in ("x", "y", "z")[:dim]:
         assert np.max(np.abs(a[f] - b[f])) < 1e-5 * h, f
 
