@@ -368,13 +368,14 @@ def job_value(n_particles, steps, t_ms, world):
     return world * n_particles * steps / (t_ms * 1e-3)
 
 
-# What bounds each site's kernel on GB300 (measured: ncu issue / stall
-# counters of the committed profiles): the PPE sweeps stream their slots from
-# HBM; the neighbour filter is instruction-issue bound; the other neighbour
-# passes wait on the latency of their gathers.
-SITE_BOUND = {"ppe_sweeps": "hbm", "filter": "issue", "density": "latency",
-              "stage1": "latency", "ppe_setup": "latency", "pgrad_gtvf": "latency",
-              "pgrad": "latency", "sort": "hbm/atomics"}
+# What bounds each site's kernel on GB300 (measured: the ncu issue and stall
+# counters of profiles/neighbour_passes_c4_issue.md): the PPE sweeps stream
+# their slots from HBM; the neighbour passes (filter, stage 1, PPE set-up,
+# pressure gradient + GTVF) issue an instruction on 64-76 % of cycles and are
+# bound by instruction issue.
+SITE_BOUND = {"ppe_sweeps": "hbm", "filter": "issue", "density": "issue",
+              "stage1": "issue", "ppe_setup": "issue", "pgrad_gtvf": "issue",
+              "pgrad": "issue", "sort": "hbm/atomics"}
 
 
 def cpu_sample(workload, cases):

@@ -390,10 +390,11 @@ __device__ __forceinline__ void count_empty_solves(const State &S) {
 // chunk's index/coefficient loads, then its CH gathers.  Longer chunks shorten the chain of dependent
 // loads behind each row (the tail of a phase waits for the longest chain),
 // fewer registers keep more blocks per SM to hide the latency of each load:
-// MIXED 3D rows (about 93 slots) take 16 at 4 blocks per SM, MIXED 2D rows
-// (25-45) 12 at 5, FP64 rows 8 at 4 (wider chunks would spill).
+// MIXED 3D rows (about 92 slots) take 16 at 4 blocks per SM, MIXED 2D rows
+// (24-44) 12 at 4 (5 blocks spill the claim of the next tile and run no
+// faster), FP64 rows 8 at 4 (wider chunks would spill).
 // ---------------------------------------------------------------------------
-constexpr int sweep_blocks_per_sm(bool mx, int ch) { return !mx ? 4 : ch >= 16 ? 4 : ch >= 12 ? 5 : 8; }
+constexpr int sweep_blocks_per_sm(bool mx, int ch) { return !mx ? 4 : ch >= 12 ? 4 : 8; }
 
 template <bool MX, int CH>
 __global__ void __launch_bounds__(256, sweep_blocks_per_sm(MX, CH)) k_sweeps(State S) {
@@ -402,6 +403,7 @@ __global__ void __launch_bounds__(256, sweep_blocks_per_sm(MX, CH)) k_sweeps(Sta
   __shared__ int flag;
   __shared__ int apre[kBalCases + 1];
   __shared__ int wsum[33];
+  __shared__ int tnext;
   const unsigned nb = gridDim.x;
   const int T = blockDim.x;
   const int nc = S.ncases;
@@ -420,6 +422,9 @@ __global__ void __launch_bounds__(256, sweep_blocks_per_sm(MX, CH)) k_sweeps(Sta
   int kcap = 0;
   for (int c = 0; c < nc; ++c) kcap = max(kcap, S.cases[c].max_iter);
   int k = 0;
+  // tickets handed out before the current F phase: in every phase each tile
+  // is claimed once and each block makes one claim past the end
+  unsigned tbase = 0u;
   for (;;) {
     const int cur = k & 1;
     R *pc = static_cast<R *>(S.pb[cur]);
@@ -485,14 +490,30 @@ __global__ void __launch_bounds__(256, sweep_blocks_per_sm(MX, CH)) k_sweeps(Sta
       const int f = __ldcg(fin + c);
       return (jacobi_case(S, c) && (f == 0 || f > k)) ? S.cases[c].nftile : 0;
     }) : S.nft;
-    for (int a = blockIdx.x; a < ntiles; a += nb) {
+    // Tiles are claimed from a grid-wide ticket counter, so a block that
+    // finishes early takes more of them; thread 0 claims the next tile while
+    // the block works on the current one.  Which block runs a tile changes
+    // nothing: its sums are per tile and the decisions add them in tile order.
+    if (threadIdx.x == 0) tnext = int(atomicAdd(&S.bar->ticket, 1u) - tbase);
+    __syncthreads();
+    int a = tnext;
+    __syncthreads();
+    while (a < ntiles) {
+      int claim = 0;
+      if (threadIdx.x == 0) claim = int(atomicAdd(&S.bar->ticket, 1u) - tbase);
       int tt = a;
       if (bal) {
         const int c = case_of_index(apre, nc, a);
         tt = S.cases[c].ftile + (a - apre[c]);
       }
       const Tile &t = S.ftiles[tt];
-      if (!bal && (__ldcg(done + t.c) || !jacobi_case(S, t.c))) continue;
+      if (!bal && (__ldcg(done + t.c) || !jacobi_case(S, t.c))) {
+        if (threadIdx.x == 0) tnext = claim;
+        __syncthreads();
+        a = tnext;
+        __syncthreads();
+        continue;
+      }
       int i = t.beg + threadIdx.x;
       R dnr = R(0), dpr = R(0);
       if (i < t.end) {
@@ -538,7 +559,12 @@ __global__ void __launch_bounds__(256, sweep_blocks_per_sm(MX, CH)) k_sweeps(Sta
         }
         __syncthreads();
       }
+      if (threadIdx.x == 0) tnext = claim;
+      __syncthreads();
+      a = tnext;
+      __syncthreads();
     }
+    tbase += unsigned(ntiles) + nb;
     alive = grid_sync(S.bar, nb, S.barrier_budget, skip);
     skip = false;
     if (!alive) break;

@@ -117,7 +117,7 @@ struct Barrier {
   unsigned count;
   unsigned gen;
   int err;
-  int pad;
+  unsigned ticket;         // fluid tiles handed out by the grid-barrier sweeps
 };
 
 // Everything a kernel may need, passed by value.  Pointers are device pointers.
