@@ -284,7 +284,7 @@ __device__ __forceinline__ R jacobi_sum(const State &S, const R *pc, int i, R ac
       load_coef<R>(S, sb, q0 + u, q0 + u < cnt, i, jj[u], cf[u]);
     R pj[8];
     _Pragma("unroll") for (int u = 0; u < 8; ++u) pj[u] = pc[jj[u]];
-    _Pragma("unroll") for (int u = 0; u < 8; ++u) acc += cf[u] * pj[u];
+    _Pragma("unroll") for (int u = 0; u < 8; ++u) acc = fma_r(cf[u], pj[u], acc);
   }
   return acc;
 }
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(256, sweep_blocks_per_sm(MX, CH)) k_sweeps(Sta
           }
           R pv[CH];
           _Pragma("unroll") for (int u = 0; u < CH; ++u) pv[u] = pc[jj[u]];
-          _Pragma("unroll") for (int u = 0; u < CH; ++u) acc += ww[u] * pv[u];
+          _Pragma("unroll") for (int u = 0; u < CH; ++u) acc = fma_r(ww[u], pv[u], acc);
         }
         R pw = acc * wsinv[r];
         if (S.cases[c].free_surface && pw < R(0)) pw = R(0);
@@ -527,10 +527,10 @@ __global__ void __launch_bounds__(256, sweep_blocks_per_sm(MX, CH)) k_sweeps(Sta
             load_coef<R>(S, sb, q0 + u, q0 + u < cnt, i, jj[u], cf[u]);
           R pj[CH];
           _Pragma("unroll") for (int u = 0; u < CH; ++u) pj[u] = pc[jj[u]];
-          _Pragma("unroll") for (int u = 0; u < CH; ++u) acc += cf[u] * pj[u];
+          _Pragma("unroll") for (int u = 0; u < CH; ++u) acc = fma_r(cf[u], pj[u], acc);
         }
         R po = pc[i];
-        R pnew = pwd[i] * acc + om1 * po;
+        R pnew = jacobi_update(pwd[i], acc, om1, po);
         pn[i] = pnew;
         dnr = fabs(pnew - po);
         dpr = fabs(pnew);
@@ -821,7 +821,7 @@ __global__ void __launch_bounds__(256, MX ? 5 : 4) k_sweeps_p2p(State S) {
       if (i < t.end) {
         R acc = jacobi_sum<R>(S, pc, i, prhs[i], S.pcnt[i]);
         R po = pc[i];
-        R pnew = pwd[i] * acc + om1 * po;
+        R pnew = jacobi_update(pwd[i], acc, om1, po);
         pn[i] = pnew;
         dnr = fabs(pnew - po);
         dpr = fabs(pnew);

@@ -132,6 +132,28 @@ __device__ __forceinline__ int case_of_index(const int *pre, int nc, int a) {
 }
 
 // ---------------------------------------------------------------------------
+// The sweep's arithmetic written out: the sweep's forms (grid barrier, point
+// to point) round alike only if each multiply-add is fused or not in the same
+// places, which a compiler left to contract a*b + c*d on its own does not
+// promise across kernels.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R fma_r(R a, R b, R c) {
+  if constexpr (std::is_same<R, float>::value) return __fmaf_rn(a, b, c);
+  else return __fma_rn(a, b, c);
+}
+template <typename R>
+__device__ __forceinline__ R mul_r(R a, R b) {
+  if constexpr (std::is_same<R, float>::value) return __fmul_rn(a, b);
+  else return __dmul_rn(a, b);
+}
+// p^{k+1} = omega/D (RHS + sum fac p^k) + (1 - omega) p^k (Eq. p-sor)
+template <typename R>
+__device__ __forceinline__ R jacobi_update(R wd, R acc, R om1, R po) {
+  return fma_r(wd, acc, mul_r(om1, po));
+}
+
+// ---------------------------------------------------------------------------
 // Stored PPE coefficients, one per ELL slot.  MIXED: the neighbour index and
 // the FP32 coefficient packed in 8 bytes, so that a sweep streams one array
 // with one load per slot; FP64: the coefficient alone (the index comes from
@@ -190,7 +212,7 @@ __device__ __forceinline__ R wall_pressure(const State &S, const R *pc, int r, i
     }
     R pv[8];
     _Pragma("unroll") for (int u = 0; u < 8; ++u) pv[u] = pc[jj[u]];
-    _Pragma("unroll") for (int u = 0; u < 8; ++u) acc += ww[u] * pv[u];
+    _Pragma("unroll") for (int u = 0; u < 8; ++u) acc = fma_r(ww[u], pv[u], acc);
   }
   R pw = acc * static_cast<const R *>(S.wsinv)[r];
   if (S.cases[c].free_surface && pw < R(0)) pw = R(0);

@@ -276,6 +276,34 @@ def test_batch_member_equals_solo(sisph, prec):
     batch.close()
 
 
+def test_batch_beyond_the_balanced_case_count(sisph):
+    """More than 1024 cases: the grid-barrier sweeps then hand out every tile
+    of the batch and skip the finished cases' instead of spreading only the
+    unfinished ones; members still equal their solo runs bit for bit."""
+    rng = np.random.Generator(np.random.PCG64(77))
+    cases = []
+    for q in range(1100):
+        if q % 2:
+            cases.append(workloads.lid_driven_cavity(int(rng.integers(11, 15)),
+                                                     re=float(rng.uniform(100, 400))))
+        else:
+            cases.append(workloads.taylor_green(int(rng.integers(11, 15)),
+                                                re=float(rng.uniform(50, 300)), tol=1e-3))
+    batch = sisph.Simulation(cases, precision=sisph.MIXED)
+    batch.step(2)
+    offs = np.cumsum([0] + [c["n"] for c in cases])
+    bst = batch.stats()
+    assert len(set(s.total_iters for s in bst)) > 1          # cases stop at different sweeps
+    for k in (0, 1, 1099):
+        solo = sisph.Simulation(cases[k], precision=sisph.MIXED)
+        solo.step(2)
+        for f in ("x", "y", "u", "v", "p"):
+            assert np.array_equal(batch.get(f)[offs[k]:offs[k + 1]], solo.get(f)), (k, f)
+        assert bst[k].total_iters == solo.stats()[0].total_iters
+        solo.close()
+    batch.close()
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("name", ["db2d", "ldc", "tgv_perturbed", "db3d"])
 def test_sweep_sync_forms_agree(sisph, prec, name):
