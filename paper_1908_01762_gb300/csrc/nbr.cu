@@ -309,13 +309,18 @@ __global__ void k_cellsort(State S) {
 // output r*, the old positions become r^n and the velocity comes from u*.
 // The rebuild position follows the particle; a marked case takes its
 // current position as the new one.
+// A case that is not rebuilt keeps its order (its particles are binned at
+// their stored rebuild positions, in the cells and in-cell order they already
+// have, and no other case's keys fall among theirs), so its particles are
+// left where they are; k_sync commits them as in a refresh without rebuild.
 template <int DIM>
 __global__ void k_gather(State S, int mode, int gather_static) {
   if (!*S.anyneed) return;
   int dst = blockIdx.x * blockDim.x + threadIdx.x;
   if (dst >= S.n) return;
-  const int src = S.perm[dst];
   const int c = S.case_of[dst];
+  if (!gather_static && !S.need[c]) return;
+  const int src = S.perm[dst];
   const bool mv = at_x(S, c);
   double uu[3] = {0, 0, 0}, tt[3] = {0, 0, 0}, xr[3] = {0, 0, 0};
   _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
@@ -362,6 +367,7 @@ __global__ void k_copyback(State S, int gather_static) {
   if (!*S.anyneed) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= S.n) return;
+  if (!gather_static && !S.need[S.case_of[i]]) return;   // not rebuilt: not gathered
   double xr[3] = {0.0, 0.0, 0.0};
   _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
     xr[k] = S.bxref[k][i];
@@ -413,6 +419,7 @@ __global__ void __launch_bounds__(256) k_skin(State S) {
   const float lx = lc[0], ly = lc[1], lz = lc[2];
   const bool exact_all = !near_cell<DIM>(pi, lc);
   const float cut2f = float(P.cut_s2) * (1.0f + 2e-4f);
+  const float cull2f = float(P.cut_s2) * (1.0f + 1e-3f);
   const double cut2d = P.cut_s2 * (1.0 + 2e-4);
   const float cutf = float(P.cut2);
   const float lo_band = cutf * (1.0f - 1e-4f), hi_band = cutf * (1.0f + 1e-4f);
@@ -447,6 +454,17 @@ __global__ void __launch_bounds__(256) k_skin(State S) {
           if (skip) continue;
           const unsigned code = stencil_code(ox, oy, oz) << kCodeShift;
           const float fx = pi.x - float(ox) * lx, fy = pi.y - float(oy) * ly, fz = pi.z - float(oz) * lz;
+          if (!exact_all) {
+            // the neighbour cell spans [o lc, (o + 1) lc) per axis around i's
+            // cell origin: skip it when its nearest point is beyond the skin
+            // radius (with a margin far above the FP32 rounding of pi)
+            const float ex = ox < 0 ? pi.x : (ox > 0 ? lx - pi.x : 0.f);
+            const float ey = oy < 0 ? pi.y : (oy > 0 ? ly - pi.y : 0.f);
+            const float ez = DIM == 3 ? (oz < 0 ? pi.z : (oz > 0 ? lz - pi.z : 0.f)) : 0.f;
+            const float e2 = fmaxf(ex, 0.f) * fmaxf(ex, 0.f) + fmaxf(ey, 0.f) * fmaxf(ey, 0.f) +
+                             fmaxf(ez, 0.f) * fmaxf(ez, 0.f);
+            if (e2 > cull2f) continue;
+          }
           const long long m = cell_key<DIM>(P, cn);
           for (int kind = k0; kind <= k1; ++kind) {
             if (kind == 1 && P.nw == 0) break;
@@ -523,17 +541,19 @@ __global__ void __launch_bounds__(256) k_skin(State S) {
 // ---------------------------------------------------------------------------
 // finish
 // ---------------------------------------------------------------------------
-// Without a rebuild the order is unchanged: mode 1 commits the stage-1
-// outputs in place (r^n <- r, r <- r*, u <- u*) and the FP32 mirrors are
-// refreshed from the FP64 state, as the gather would have done.  Always: the
-// FP32 relative positions at X.
+// Without a rebuild of the particle's case its order is unchanged: mode 1
+// commits the stage-1 outputs in place (r^n <- r, r <- r*, u <- u*) and the
+// FP32 mirrors are refreshed from the FP64 state, as the gather would have
+// done.  Always: the FP32 relative positions at X.
 template <int DIM>
 __global__ void k_sync(State S, int mode) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= S.n) return;
-  const CaseDev &P = S.cases[S.case_of[i]];
+  const int c = S.case_of[i];
+  const CaseDev &P = S.cases[c];
   double xi[3] = {0, 0, 0};
-  if (*S.anyneed) {
+  if (*S.anyneed && S.need[c]) {
+    // rebuilt: the gather has committed the state in the new order
     _Pragma("unroll") for (int k = 0; k < DIM; ++k) xi[k] = S.x[k][i];
     S.pf4[i] = rel_pos<DIM>(P, xi, S.cell[i], S.m[i]);
     return;
