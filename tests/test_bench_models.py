@@ -70,3 +70,28 @@ def test_launch_options_follow_the_tune_flag(tmp_path, monkeypatch):
     assert note == {"source": "autotune cache", **opts}
     # the shipped cache is what the benchmark reads by default
     assert os.path.dirname(autotune.DEFAULT_CACHE) == os.path.join(ROOT, "paper_1908_01762_gb300")
+
+
+def test_cpu_sample_keeps_the_workloads_resolution():
+    # the oracle is timed on a bounded sample of the same dam break: the same
+    # dx and physics, tank and column scaled by 1/4 per axis (about 1/64 of
+    # the particles); the batch on its first case
+    import workloads
+    big = workloads.dam_break_3d(dx=0.00524)
+    sample, what = bench.cpu_sample("c4l", [big])
+    assert sample["params"]["h"] == big["params"]["h"]
+    assert sample["params"]["rho0"] == big["params"]["rho0"] and sample["dim"] == 3
+    nf_big = int(np.sum(big["kind"] == 0))
+    nf = int(np.sum(sample["kind"] == 0))
+    assert 0.7 / 64 < nf / nf_big < 1.3 / 64
+    assert "1/4" in what
+    cases = workloads.batch_ensemble(64)
+    sample, what = bench.cpu_sample("c5", cases)
+    assert sample is cases[0]
+
+
+def test_step_bytes_sums_the_modelled_sites():
+    sites = {"ppe_sweeps": {"launches_per_step": 1.0}, "filter": {"launches_per_step": 2.0},
+             "sync": {"launches_per_step": 2.0}}
+    fb = bench.kernel_bytes("filter", True, 3, 7, 10, 50, 60, 90)
+    assert bench.step_bytes(sites, 1000.0, True, 3, 7, 10, 50, 60, 90) == 1000.0 + 2 * fb
