@@ -586,9 +586,9 @@ def e2e_leg(cases, prec, args, torch, world, stream):
     """The same metric over the same steps through the C-ABI with host
     buffers: a new handle of the workload takes the same untimed warm-up
     steps; then every timed step copies the whole state from pinned host
-    memory to the device (sisph_set), advances one step and reads the whole
-    state back (sisph_get).  The copies move more than the L2 holds, so no
-    extra flush is written."""
+    memory to the device (one sisph_set_many call), advances one step and
+    reads the whole state back (one sisph_get_many call).  The copies move
+    more than the L2 holds, so no extra flush is written."""
     from paper_1908_01762_gb300 import sisph
     sim = sisph.Simulation(cases, precision=prec, use_graph=0 if args.no_graph else 1,
                            **args.launch_opts)
@@ -605,12 +605,11 @@ def e2e_leg(cases, prec, args, torch, world, stream):
     if world > 1:
         torch.distributed.barrier()
     t0 = time.perf_counter()
+    arrays = [host[f] for f in fields]
     for _ in range(args.steps):
-        for f in fields:
-            sim.set(f, host[f])
+        sim.set_many(fields, arrays)
         sim.step(1)
-        for f in fields:
-            sisph.sisph_get(sim.h, f, n, host[f])
+        sim.get_many(fields, arrays)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     sim.close()

@@ -1089,62 +1089,128 @@ int sisph_step(sisph_t s, int32_t nsteps) {
   return rc;
 }
 
-int sisph_get(sisph_t s, int32_t field, double *out) {
-  if (!valid_handle(s) || !out) return fail(s, SISPH_EINVAL, "invalid handle or output");
+// Device source of a readable field (nullptr for the GTVF displacement,
+// which is scattered from its own buffers); false for an unknown field.
+static bool get_source(sisph_t s, int32_t field, const void **src) {
+  State &S = s->S;
+  *src = nullptr;
+  switch (field) {
+    case SISPH_F_X: case SISPH_F_Y: case SISPH_F_Z: *src = S.x[field - SISPH_F_X]; return true;
+    case SISPH_F_U: case SISPH_F_V: case SISPH_F_W: *src = S.u[field - SISPH_F_U]; return true;
+    case SISPH_F_UT: case SISPH_F_VT: case SISPH_F_WT: *src = S.ut[field - SISPH_F_UT]; return true;
+    case SISPH_F_P: *src = S.p; return true;
+    case SISPH_F_RHO: *src = S.rho; return true;
+    case SISPH_F_M: *src = S.m; return true;
+    case SISPH_F_NX: case SISPH_F_NY: case SISPH_F_NZ: *src = S.nrm[field - SISPH_F_NX]; return true;
+    case SISPH_F_RHS: *src = S.rhs_out; return true;
+    case SISPH_F_DIAG: *src = S.diag_out; return true;
+    case SISPH_F_DX: case SISPH_F_DY: case SISPH_F_DZ: return true;
+    case SISPH_F_NSKIN: *src = S.sncnt; return true;
+    case SISPH_F_NCOUNT: *src = S.ncnt; return true;
+    default: return false;
+  }
+}
+
+// Scatter one field into caller order in d_tmp and queue its copy to out.
+static cudaError_t queue_get(sisph_t s, int32_t field, const void *src, double *out) {
   State &S = s->S;
   Launch L = mk_launch(s);
   L.before = nullptr;
   L.after = nullptr;
-  cudaError_t e = cudaSuccess;
-  const void *src = nullptr;
-  switch (field) {
-    case SISPH_F_X: case SISPH_F_Y: case SISPH_F_Z: src = S.x[field - SISPH_F_X]; break;
-    case SISPH_F_U: case SISPH_F_V: case SISPH_F_W: src = S.u[field - SISPH_F_U]; break;
-    case SISPH_F_UT: case SISPH_F_VT: case SISPH_F_WT: src = S.ut[field - SISPH_F_UT]; break;
-    case SISPH_F_P: src = S.p; break;
-    case SISPH_F_RHO: src = S.rho; break;
-    case SISPH_F_M: src = S.m; break;
-    case SISPH_F_NX: case SISPH_F_NY: case SISPH_F_NZ: src = S.nrm[field - SISPH_F_NX]; break;
-    case SISPH_F_RHS: src = S.rhs_out; break;
-    case SISPH_F_DIAG: src = S.diag_out; break;
-    case SISPH_F_DX: case SISPH_F_DY: case SISPH_F_DZ: break;
-    case SISPH_F_NSKIN: src = S.sncnt; break;
-    case SISPH_F_NCOUNT: src = S.ncnt; break;
-    default: return fail(s, SISPH_EINVAL, "unknown field");
-  }
+  cudaError_t e;
   if (field >= SISPH_F_DX && field <= SISPH_F_DZ) e = launch_scatter_disp(S, L, field - SISPH_F_DX, s->d_tmp);
   else if (field == SISPH_F_NSKIN || field == SISPH_F_NCOUNT) e = launch_scatter_field(S, L, src, 2, 0, 0, s->d_tmp);
   else e = launch_scatter_field(S, L, src, 0, 0, 0, s->d_tmp);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, s->d_tmp, size_t(s->n) * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  return e;
+}
+
+int sisph_get(sisph_t s, int32_t field, double *out) {
+  if (!valid_handle(s) || !out) return fail(s, SISPH_EINVAL, "invalid handle or output");
+  const void *src = nullptr;
+  if (!get_source(s, field, &src)) return fail(s, SISPH_EINVAL, "unknown field");
+  cudaError_t e = queue_get(s, field, src, out);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "get");
   return SISPH_OK;
 }
 
-int sisph_set(sisph_t s, int32_t field, const double *in) {
-  if (!valid_handle(s) || !in) return fail(s, SISPH_EINVAL, "invalid handle or input");
+int sisph_get_many(sisph_t s, int32_t nfields, const int32_t *fields, double *const *out) {
+  if (!valid_handle(s) || nfields < 0 || (nfields > 0 && (!fields || !out)))
+    return fail(s, SISPH_EINVAL, "invalid handle, count or arrays");
+  std::vector<const void *> src(size_t(std::max(nfields, 1)));
+  for (int k = 0; k < nfields; ++k) {
+    if (!out[k]) return fail(s, SISPH_EINVAL, "a NULL output array");
+    if (!get_source(s, fields[k], &src[k])) return fail(s, SISPH_EINVAL, "unknown field");
+  }
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < nfields && e == cudaSuccess; ++k) e = queue_get(s, fields[k], src[k], out[k]);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "get_many");
+  return SISPH_OK;
+}
+
+// Device destination of a writable field; false for an unknown or read-only
+// field or a third component in 2D.
+static bool set_target(sisph_t s, int32_t field, double **dst) {
   State &S = s->S;
+  *dst = nullptr;
+  switch (field) {
+    case SISPH_F_X: case SISPH_F_Y: case SISPH_F_Z: *dst = S.x[field - SISPH_F_X]; break;
+    case SISPH_F_U: case SISPH_F_V: case SISPH_F_W: *dst = S.u[field - SISPH_F_U]; break;
+    case SISPH_F_UT: case SISPH_F_VT: case SISPH_F_WT: *dst = S.ut[field - SISPH_F_UT]; break;
+    case SISPH_F_P: *dst = S.p; break;
+    case SISPH_F_RHO: *dst = S.rho; break;
+    default: return false;
+  }
+  if ((field == SISPH_F_Z || field == SISPH_F_W || field == SISPH_F_WT) && s->dim == 2) return false;
+  return true;
+}
+
+// Queue the copy of one field into d_tmp and its gather into the sorted
+// order (the stream orders the next copy after this gather).
+static cudaError_t queue_set(sisph_t s, int32_t field, double *dst, const double *in) {
   Launch L = mk_launch(s);
   L.before = nullptr;
   L.after = nullptr;
-  double *dst = nullptr;
-  switch (field) {
-    case SISPH_F_X: case SISPH_F_Y: case SISPH_F_Z: dst = S.x[field - SISPH_F_X]; break;
-    case SISPH_F_U: case SISPH_F_V: case SISPH_F_W: dst = S.u[field - SISPH_F_U]; break;
-    case SISPH_F_UT: case SISPH_F_VT: case SISPH_F_WT: dst = S.ut[field - SISPH_F_UT]; break;
-    case SISPH_F_P: dst = S.p; break;
-    case SISPH_F_RHO: dst = S.rho; break;
-    default: return fail(s, SISPH_EINVAL, "field is read-only or unknown");
-  }
-  if ((field == SISPH_F_Z || field == SISPH_F_W || field == SISPH_F_WT) && s->dim == 2)
-    return fail(s, SISPH_EINVAL, "no third component in 2D");
   cudaError_t e = cudaMemcpyAsync(s->d_tmp, in, size_t(s->n) * sizeof(double), cudaMemcpyHostToDevice, s->stream);
   // positions: fluid that moved past half the skin is re-sorted by the next
   // refresh's own check; a wall that moved forces every case to be rebuilt
-  if (e == cudaSuccess) e = launch_gather_field(S, L, s->d_tmp, dst, field <= SISPH_F_Z);
-  if (e == cudaSuccess) e = launch_refresh_mirrors(S, L);
+  if (e == cudaSuccess) e = launch_gather_field(s->S, L, s->d_tmp, dst, field <= SISPH_F_Z);
+  return e;
+}
+
+int sisph_set(sisph_t s, int32_t field, const double *in) {
+  if (!valid_handle(s) || !in) return fail(s, SISPH_EINVAL, "invalid handle or input");
+  double *dst = nullptr;
+  if (!set_target(s, field, &dst)) return fail(s, SISPH_EINVAL, "field is read-only, unknown or not in 2D");
+  Launch L = mk_launch(s);
+  L.before = nullptr;
+  L.after = nullptr;
+  cudaError_t e = queue_set(s, field, dst, in);
+  if (e == cudaSuccess) e = launch_refresh_mirrors(s->S, L);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "set");
+  return SISPH_OK;
+}
+
+int sisph_set_many(sisph_t s, int32_t nfields, const int32_t *fields, const double *const *in) {
+  if (!valid_handle(s) || nfields < 0 || (nfields > 0 && (!fields || !in)))
+    return fail(s, SISPH_EINVAL, "invalid handle, count or arrays");
+  std::vector<double *> dst(size_t(std::max(nfields, 1)));
+  for (int k = 0; k < nfields; ++k) {
+    if (!in[k]) return fail(s, SISPH_EINVAL, "a NULL input array");
+    if (!set_target(s, fields[k], &dst[k]))
+      return fail(s, SISPH_EINVAL, "field is read-only, unknown or not in 2D");
+  }
+  Launch L = mk_launch(s);
+  L.before = nullptr;
+  L.after = nullptr;
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < nfields && e == cudaSuccess; ++k) e = queue_set(s, fields[k], dst[k], in[k]);
+  if (e == cudaSuccess && nfields > 0) e = launch_refresh_mirrors(s->S, L);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "set_many");
   return SISPH_OK;
 }
 

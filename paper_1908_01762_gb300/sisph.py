@@ -99,6 +99,8 @@ def load_library(path: str = None):
         "sisph_batch_step": (C.c_int, [h, C.c_int32, _ip]),
         "sisph_get": (C.c_int, [h, C.c_int32, _dp]),
         "sisph_set": (C.c_int, [h, C.c_int32, _dp]),
+        "sisph_get_many": (C.c_int, [h, C.c_int32, _ip, C.POINTER(_dp)]),
+        "sisph_set_many": (C.c_int, [h, C.c_int32, _ip, C.POINTER(_dp)]),
         "sisph_stats": (C.c_int, [h, C.POINTER(sisph_case_stats)]),
         "sisph_info": (C.c_int, [h, C.POINTER(C.c_int64), C.POINTER(C.c_int64), _ip, _ip]),
         "sisph_set_stream": (C.c_int, [h, C.c_void_p]),
@@ -245,6 +247,28 @@ def sisph_set(h, field, values):
                                     a.ctypes.data_as(_dp)), h)
 
 
+def _field_ids(fields):
+    return np.ascontiguousarray([FIELDS[f] if isinstance(f, str) else int(f) for f in fields], np.int32)
+
+
+def sisph_set_many(h, fields, arrays):
+    """Write several fields in one call (arrays: n doubles each, caller's
+    order; page-locked arrays copy asynchronously)."""
+    ids = _field_ids(fields)
+    arrs = [np.ascontiguousarray(a, np.float64) for a in arrays]
+    ptrs = (_dp * max(1, len(arrs)))(*[a.ctypes.data_as(_dp) for a in arrs])
+    _check(load_library().sisph_set_many(h, len(arrs), ids.ctypes.data_as(_ip), ptrs), h)
+
+
+def sisph_get_many(h, fields, n, outs=None):
+    """Read several fields in one call into `outs` (new arrays if None)."""
+    ids = _field_ids(fields)
+    outs = [np.empty(n, np.float64) for _ in fields] if outs is None else outs
+    ptrs = (_dp * max(1, len(outs)))(*[o.ctypes.data_as(_dp) for o in outs])
+    _check(load_library().sisph_get_many(h, len(outs), ids.ctypes.data_as(_ip), ptrs), h)
+    return outs
+
+
 def sisph_neighbors(h, n):
     L = load_library()
     counts = np.zeros(n, np.int32)
@@ -369,6 +393,12 @@ class Simulation:
 
     def set(self, field, values):
         sisph_set(self.h, field, values)
+
+    def get_many(self, fields, outs=None):
+        return sisph_get_many(self.h, fields, self.n, outs)
+
+    def set_many(self, fields, arrays):
+        sisph_set_many(self.h, fields, arrays)
 
     def step(self, nsteps=1):
         return sisph_step(self.h, nsteps)

@@ -104,6 +104,10 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.sisph_step(None, 1) == sisph.EINVAL
     assert lib.sisph_get(None, 0, buf.ctypes.data_as(C.POINTER(C.c_double))) == sisph.EINVAL
     assert lib.sisph_build_neighbors(None) == sisph.EINVAL
+    ids = np.zeros(1, np.int32)
+    ptrs = (C.POINTER(C.c_double) * 1)(buf.ctypes.data_as(C.POINTER(C.c_double)))
+    assert lib.sisph_get_many(None, 1, ids.ctypes.data_as(C.POINTER(C.c_int32)), ptrs) == sisph.EINVAL
+    assert lib.sisph_set_many(None, 1, ids.ctypes.data_as(C.POINTER(C.c_int32)), ptrs) == sisph.EINVAL
     lib.sisph_destroy(None)
 
 
