@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256, MX ? 6 : 3) k_density(State S) {
     int j;
     R d[3];
     R r2 = G.pair(S, P, K.lc, e, j, d);
-    R w = mass<MX>(S, j) * poly_w<R>(qof<R>(sqrt_r(r2), K.h, K.ih));
+    R w = mass<MX>(S, j) * poly_w<R>(qof<R>(sqrt_x(r2), K.h, K.ih));
     acc += valid ? w : R(0);
   })
   acc *= K.sig;
@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(256, 5) k_pgrad_gtvf1(State S) {
       float4 pj4 = S.pf4[j];
       float d[3];
       float r2 = pair_f<DIM>(K.lc, pi4, pj4, e >> kCodeShift, d);
-      float r = sqrtf(r2);
+      float r = sqrt_r(r2);
       float rj = S.vf4[j].w, mj = pj4.w, pj = S.pf[j];
       float fr = r > 0.f ? divr(K.dsc * poly_dw<float>(qof<float>(r, K.h, K.ih)), r) : 0.f;
       float c = symm ? -mj * (pri + divr(pj, rj * rj)) : -divr(mj * (pj - pi), rj) * iri;

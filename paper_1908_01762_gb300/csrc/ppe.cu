@@ -381,11 +381,22 @@ __device__ __forceinline__ void count_empty_solves(const State &S) {
 //     completes the last tile of a case (per-case arrival counter) applies
 //     Eq. convergence (decide_case).
 //   grid barrier after each phase.
+// Tail: once the unfinished cases have fewer fluid tiles than the grid has
+// blocks (and at most kBalCases cases), block a owns the a-th of those tiles
+// for the rest of the solve and every case runs its remaining sweeps on its
+// own: the owners of a case meet at a per-case barrier after each phase
+// (the F barrier is the arrival counter itself, released by the block that
+// decides), split the case's wall rows among them, and publish what they
+// wrote once the case stops; the other blocks publish the cases that had
+// already stopped and leave.  No grid barrier runs in the tail, and a case
+// that converges early no longer waits for the slowest one.  Every row and
+// every decision is computed as in the phases above, so the result is the
+// same bit for bit.
 // p^k lives in buffer k&1.  Pressures written by other blocks are read with
-// ordinary (L1-cached) loads: every grid barrier ends with an acquire fence
-// in the block's master thread followed by a block barrier, which orders
-// those reads after the other blocks' writes.  Flags and partial sums are
-// read with ld.global.cg.
+// ordinary (L1-cached) loads: every grid (or per-case) barrier ends with an
+// acquire fence in the block's master thread followed by a block barrier,
+// which orders those reads after the other blocks' writes.  Flags and
+// partial sums are read with ld.global.cg.
 // A fluid row's slots (and a wall row's entries) go in chunks of CH: the
 // chunk's index/coefficient loads, then its CH gathers.  Longer chunks shorten the chain of dependent
 // loads behind each row (the tail of a phase waits for the longest chain),
@@ -396,9 +407,191 @@ __device__ __forceinline__ void count_empty_solves(const State &S) {
 // ---------------------------------------------------------------------------
 constexpr int sweep_blocks_per_sm(bool mx, int ch) { return !mx ? 4 : ch >= 12 ? 4 : 8; }
 
+template <bool MX>
+using SweepReal = typename std::conditional<MX, float, double>::type;
+
+// Row i of Eq. p-sor: p^{k+1}_i into pn from p^k in pc; dnr, dpr receive
+// |p^{k+1}_i - p^k_i| and |p^{k+1}_i|.
+template <bool MX, int CH>
+__device__ __forceinline__ void sweep_row(const State &S, int i, const SweepReal<MX> *pc,
+                                          SweepReal<MX> *pn, SweepReal<MX> om1, SweepReal<MX> &dnr,
+                                          SweepReal<MX> &dpr) {
+  using R = SweepReal<MX>;
+  R acc = static_cast<const R *>(S.prhs)[i];
+  const int cnt = S.pcnt[i];
+  const long long sb = slot_base(S, i);
+  for (int q0 = 0; q0 < cnt; q0 += CH) {
+    int jj[CH];
+    R cf[CH];
+    _Pragma("unroll") for (int u = 0; u < CH; ++u)
+      load_coef<R>(S, sb, q0 + u, q0 + u < cnt, i, jj[u], cf[u]);
+    R pj[CH];
+    _Pragma("unroll") for (int u = 0; u < CH; ++u) pj[u] = pc[jj[u]];
+    _Pragma("unroll") for (int u = 0; u < CH; ++u) acc = fma_r(cf[u], pj[u], acc);
+  }
+  const R po = pc[i];
+  const R pnew = jacobi_update(static_cast<const R *>(S.pwd)[i], acc, om1, po);
+  pn[i] = pnew;
+  dnr = fabs(pnew - po);
+  dpr = fabs(pnew);
+}
+
+// Master thread: wait until the per-case generation counter leaves g0.
+// false after the barrier budget (the timeout flag is raised) or when
+// another block has raised an error.
+__device__ __forceinline__ bool case_wait(const State &S, const unsigned *gen, unsigned g0) {
+  volatile const unsigned *vg = gen;
+  volatile const int *verr = &S.bar->err;
+  const long long t0 = clock64();
+  while (*vg == g0) {
+    if (*verr) return false;
+    if (clock64() - t0 > S.barrier_budget) {
+      atomicExch(&S.bar->err, kErrTimeout);
+      return false;
+    }
+    __nanosleep(32);
+  }
+  return true;
+}
+
+// Final pressure of row i from buffer b into the FP64 state (and its FP32
+// mirror).
+template <bool MX>
+__device__ __forceinline__ void publish_row(const State &S, int i, int b) {
+  const SweepReal<MX> v = __ldcg(static_cast<const SweepReal<MX> *>(S.pb[b]) + i);
+  S.p[i] = double(v);
+  if constexpr (MX) S.pf[i] = v;
+}
+
+// The tail of the grid-barrier solve from F phase k on (see above).  apre is
+// the prefix of the unfinished cases' fluid tiles at that point (ntiles in
+// all, fewer than the grid's blocks).  Returns false when a wait failed (the
+// error word is set).
+template <bool MX, int CH>
+__device__ __forceinline__ bool sweep_tail(const State &S, const int *apre, int ntiles, int k, int kcap,
+                                           bool skip, double *sh, int *shv) {
+  using R = SweepReal<MX>;
+  // chunks of at most 12 here: the tail's own state would otherwise push
+  // the 16-wide 3D rows past the kernel's registers (the sums do not depend
+  // on the chunk width)
+  constexpr int CT = CH < 12 ? CH : 12;
+  const int T = blockDim.x;
+  const int nc = S.ncases;
+  const R om1 = R(1.0 - S.omega);
+  int *done = S.act;
+  int *fin = S.act + nc;
+  unsigned *arrive = reinterpret_cast<unsigned *>(S.par + nc);       // [nc]
+  unsigned *wbar = reinterpret_cast<unsigned *>(S.par + 2 * nc);     // [nc] wall-phase arrivals
+  unsigned *gen = reinterpret_cast<unsigned *>(S.par + 3 * nc);      // [nc] barrier generations
+  if (int(blockIdx.x) >= ntiles) {
+    // cases that stopped before the tail (or never swept) are final:
+    // their last writes came before the grid barrier that preceded it
+    for (int i = (int(blockIdx.x) - ntiles) * T + threadIdx.x; i < S.n;
+         i += (int(gridDim.x) - ntiles) * T) {
+      const int c = S.case_of[i];
+      if (!jacobi_case(S, c) || apre[c + 1] > apre[c]) continue;
+      publish_row<MX>(S, i, __ldcg(S.par + c));
+    }
+    return true;
+  }
+  const int a = blockIdx.x;
+  const int c = case_of_index(apre, nc, a);
+  const int q = a - apre[c];                 // this block's rank among the case's owners
+  const CaseDev &P = S.cases[c];
+  const int m = P.nftile;                    // owners: every fluid tile of the case
+  const int tt = P.ftile + q;
+  const Tile &t = S.ftiles[tt];
+  const int i = t.beg + threadIdx.x;
+  int kk = k;
+  int stop = 0;                              // sweep count at which the case stopped
+  for (;;) {
+    const R *pc = static_cast<const R *>(S.pb[kk & 1]);
+    R *pn = static_cast<R *>(S.pb[(kk & 1) ^ 1]);
+    // ---- F(kk) on the owned tile; arrival, decision and release ----
+    R dnr = R(0), dpr = R(0);
+    if (i < t.end) sweep_row<MX, CT>(S, i, pc, pn, om1, dnr, dpr);
+    double dn, dp;
+    tile_sums<MX>(dn, dp, sh, dnr, dpr);
+    unsigned g0 = 0u;
+    if (threadIdx.x == 0) {
+      S.tile_part[2 * tt] = dn;
+      S.tile_part[2 * tt + 1] = dp;
+      g0 = *reinterpret_cast<volatile unsigned *>(gen + c);
+      __threadfence();
+      *shv = skip ? 0 : (atomicAdd(arrive + c, 1u) == unsigned(m - 1));
+    }
+    __syncthreads();
+    const bool decider = *shv != 0;
+    __syncthreads();
+    if (decider) {
+      __threadfence();
+      const int stop_at = decide_case(S, c, kk, S.tile_part, sh, 2);
+      if (threadIdx.x == 0) {
+        arrive[c] = 0u;
+        if (stop_at) {
+          fin[c] = stop_at;
+          __threadfence();
+          done[c] = 1;
+        }
+        __threadfence();
+        atomicAdd(gen + c, 1u);
+        *shv = stop_at;
+      }
+    } else if (threadIdx.x == 0) {
+      const bool ok = case_wait(S, gen + c, g0);
+      __threadfence();
+      *shv = ok ? __ldcg(fin + c) : -1;
+    }
+    __syncthreads();
+    stop = *shv;
+    __syncthreads();
+    if (stop < 0) return false;
+    skip = false;
+    ++kk;
+    // ---- W(kk): the case's wall rows, split over its owners (the final
+    // wall update when the case has just stopped) ----
+    R *pw = static_cast<R *>(S.pb[kk & 1]);
+    for (int rr = q * T + threadIdx.x; rr < P.nw; rr += m * T) {
+      const int r = P.wrow + rr;
+      const int w = S.wall_at[r];
+      pw[w] = wall_pressure<R, CT>(S, pw, r, w, c);
+    }
+    if (stop) break;
+    if (P.nw > 0) {
+      if (threadIdx.x == 0) {
+        g0 = *reinterpret_cast<volatile unsigned *>(gen + c);
+        __threadfence();
+        bool ok = true;
+        if (atomicAdd(wbar + c, 1u) == unsigned(m - 1)) {
+          wbar[c] = 0u;
+          __threadfence();
+          atomicAdd(gen + c, 1u);
+        } else {
+          ok = case_wait(S, gen + c, g0);
+        }
+        __threadfence();
+        *shv = ok ? 1 : 0;
+      }
+      __syncthreads();
+      const bool ok = *shv != 0;
+      __syncthreads();
+      if (!ok) return false;
+    }
+    if (kk >= kcap) {
+      if (threadIdx.x == 0) atomicOr(S.err, kErrNotConv);
+      return true;
+    }
+  }
+  // ---- publish what this block wrote last: its fluid rows (F(stop-1))
+  // and its share of the wall rows (W(stop)), both in buffer stop & 1 ----
+  if (i < t.end) publish_row<MX>(S, i, stop & 1);
+  for (int rr = q * T + threadIdx.x; rr < P.nw; rr += m * T) publish_row<MX>(S, S.wall_at[P.wrow + rr], stop & 1);
+  return true;
+}
+
 template <bool MX, int CH>
 __global__ void __launch_bounds__(256, sweep_blocks_per_sm(MX, CH)) k_sweeps(State S) {
-  using R = typename std::conditional<MX, float, double>::type;
+  using R = SweepReal<MX>;
   __shared__ double sh[64];
   __shared__ int flag;
   __shared__ int apre[kBalCases + 1];
@@ -408,16 +601,11 @@ __global__ void __launch_bounds__(256, sweep_blocks_per_sm(MX, CH)) k_sweeps(Sta
   const int T = blockDim.x;
   const int nc = S.ncases;
   const R om1 = R(1.0 - S.omega);
-  const R *prhs = static_cast<const R *>(S.prhs);
-  const R *pwd = static_cast<const R *>(S.pwd);
-  const R *wc = static_cast<const R *>(S.wcoef);
-  const R *wsinv = static_cast<const R *>(S.wsinv);
-  const R *wh = static_cast<const R *>(S.wh);
   int *done = S.act;                 // [nc] case finished
   int *fin = S.act + nc;             // [nc] sweep count at which it finished
   unsigned *arrive = reinterpret_cast<unsigned *>(S.par + nc);  // [nc]
   bool skip = S.debug_skip_barrier && blockIdx.x == 1;
-  bool alive = true;
+  bool alive = true, tail = false;
   // hard bound on the loop: every case stops at its max_iter at the latest
   int kcap = 0;
   for (int c = 0; c < nc; ++c) kcap = max(kcap, S.cases[c].max_iter);
@@ -446,25 +634,7 @@ __global__ void __launch_bounds__(256, sweep_blocks_per_sm(MX, CH)) k_sweeps(Sta
         int w = S.wall_at[r];
         int c = S.case_of[w];
         if (!bal && (!jacobi_case(S, c) || (k > 0 && __ldcg(done + c) && __ldcg(fin + c) != k))) continue;
-        R acc = wh[r];
-        const int cnt = S.wcnt[r];
-        for (int q0 = 0; q0 < cnt; q0 += CH) {
-          int jj[CH];
-          R ww[CH];
-          _Pragma("unroll") for (int u = 0; u < CH; ++u) {
-            const int q = q0 + u;
-            const long long o = ell_at(S.wcap, q, r);
-            jj[u] = q < cnt ? S.widx[o] : w;
-            ww[u] = q < cnt ? wc[o] : R(0);
-            SISPH_CHECK_IDX(S, jj[u], w);
-          }
-          R pv[CH];
-          _Pragma("unroll") for (int u = 0; u < CH; ++u) pv[u] = pc[jj[u]];
-          _Pragma("unroll") for (int u = 0; u < CH; ++u) acc = fma_r(ww[u], pv[u], acc);
-        }
-        R pw = acc * wsinv[r];
-        if (S.cases[c].free_surface && pw < R(0)) pw = R(0);
-        pc[w] = pw;
+        pc[w] = wall_pressure<R, CH>(S, pc, r, w, c);
       }
       alive = grid_sync(S.bar, nb, S.barrier_budget, skip);
       skip = false;
@@ -490,6 +660,13 @@ __global__ void __launch_bounds__(256, sweep_blocks_per_sm(MX, CH)) k_sweeps(Sta
       const int f = __ldcg(fin + c);
       return (jacobi_case(S, c) && (f == 0 || f > k)) ? S.cases[c].nftile : 0;
     }) : S.nft;
+    // fewer tiles than blocks: the tail (every block takes the same branch,
+    // since all read the same stop counts after the grid barrier)
+    if (bal && ntiles < int(nb)) {
+      alive = sweep_tail<MX, CH>(S, apre, ntiles, k, kcap, skip, sh, &flag);
+      tail = true;
+      break;
+    }
     // Tiles are claimed from a grid-wide ticket counter, so a block that
     // finishes early takes more of them; thread 0 claims the next tile while
     // the block works on the current one.  Which block runs a tile changes
@@ -516,25 +693,7 @@ __global__ void __launch_bounds__(256, sweep_blocks_per_sm(MX, CH)) k_sweeps(Sta
       }
       int i = t.beg + threadIdx.x;
       R dnr = R(0), dpr = R(0);
-      if (i < t.end) {
-        R acc = prhs[i];
-        const int cnt = S.pcnt[i];
-        const long long sb = slot_base(S, i);
-        for (int q0 = 0; q0 < cnt; q0 += CH) {
-          int jj[CH];
-          R cf[CH];
-          _Pragma("unroll") for (int u = 0; u < CH; ++u)
-            load_coef<R>(S, sb, q0 + u, q0 + u < cnt, i, jj[u], cf[u]);
-          R pj[CH];
-          _Pragma("unroll") for (int u = 0; u < CH; ++u) pj[u] = pc[jj[u]];
-          _Pragma("unroll") for (int u = 0; u < CH; ++u) acc = fma_r(cf[u], pj[u], acc);
-        }
-        R po = pc[i];
-        R pnew = jacobi_update(pwd[i], acc, om1, po);
-        pn[i] = pnew;
-        dnr = fabs(pnew - po);
-        dpr = fabs(pnew);
-      }
+      if (i < t.end) sweep_row<MX, CH>(S, i, pc, pn, om1, dnr, dpr);
       double dn, dp;
       tile_sums<MX>(dn, dp, sh, dnr, dpr);
       if (threadIdx.x == 0) {
@@ -571,14 +730,13 @@ __global__ void __launch_bounds__(256, sweep_blocks_per_sm(MX, CH)) k_sweeps(Sta
     ++k;
   }
   if (!alive) return;
-  // ---- publish the final pressure of every case ----
-  for (int i = blockIdx.x * T + threadIdx.x; i < S.n; i += nb * T) {
-    int c = S.case_of[i];
-    if (!jacobi_case(S, c)) continue;
-    R v = __ldcg(static_cast<const R *>(S.pb[__ldcg(S.par + c)]) + i);
-    S.p[i] = double(v);
-    if constexpr (MX) S.pf[i] = v;
-  }
+  // ---- publish the final pressure of every case (the tail has published
+  // its cases itself) ----
+  if (!tail)
+    for (int i = blockIdx.x * T + threadIdx.x; i < S.n; i += nb * T) {
+      const int c = S.case_of[i];
+      if (jacobi_case(S, c)) publish_row<MX>(S, i, __ldcg(S.par + c));
+    }
   if (blockIdx.x == 0) count_empty_solves(S);
 }
 

@@ -192,27 +192,28 @@ __device__ __forceinline__ void load_coef(const State &S, long long base, int q,
 
 // ---------------------------------------------------------------------------
 // One wall row of Eq. p-shepard: p_w = (sum_f p_f W_wf + H_w) / sum_f W_wf,
-// clamped at 0 in free-surface flows.  Chunks of 8: the index and weight
-// loads go out together, then the 8 pressure gathers.
+// clamped at 0 in free-surface flows.  Chunks of CH: the index and weight
+// loads go out together, then the CH pressure gathers; the sum runs over the
+// entries in order whatever CH is.
 // ---------------------------------------------------------------------------
-template <typename R>
+template <typename R, int CH = 8>
 __device__ __forceinline__ R wall_pressure(const State &S, const R *pc, int r, int w, int c) {
   const R *wc = static_cast<const R *>(S.wcoef);
   R acc = static_cast<const R *>(S.wh)[r];
   const int cnt = S.wcnt[r];
-  for (int q0 = 0; q0 < cnt; q0 += 8) {
-    int jj[8];
-    R ww[8];
-    _Pragma("unroll") for (int u = 0; u < 8; ++u) {
+  for (int q0 = 0; q0 < cnt; q0 += CH) {
+    int jj[CH];
+    R ww[CH];
+    _Pragma("unroll") for (int u = 0; u < CH; ++u) {
       const int q = q0 + u;
       const long long o = ell_at(S.wcap, q, r);
       jj[u] = q < cnt ? S.widx[o] : w;
       ww[u] = q < cnt ? wc[o] : R(0);
       SISPH_CHECK_IDX(S, jj[u], w);
     }
-    R pv[8];
-    _Pragma("unroll") for (int u = 0; u < 8; ++u) pv[u] = pc[jj[u]];
-    _Pragma("unroll") for (int u = 0; u < 8; ++u) acc = fma_r(ww[u], pv[u], acc);
+    R pv[CH];
+    _Pragma("unroll") for (int u = 0; u < CH; ++u) pv[u] = pc[jj[u]];
+    _Pragma("unroll") for (int u = 0; u < CH; ++u) acc = fma_r(ww[u], pv[u], acc);
   }
   R pw = acc * static_cast<const R *>(S.wsinv)[r];
   if (S.cases[c].free_surface && pw < R(0)) pw = R(0);

@@ -265,8 +265,21 @@ struct KC {
   }
 };
 
+// |r_ij| from |r_ij|^2 in a neighbour sum.  FP64: the correctly rounded
+// square root.  FP32 (MIXED): r^2 times its approximate reciprocal square
+// root (rsqrtf, relative error about 1e-7, far inside the FP32 error budget
+// of those sums and a few instructions where the rounded root takes a
+// dozen), 0 at r^2 = 0.
 template <typename R>
 __device__ __forceinline__ R sqrt_r(R v) {
+  if constexpr (std::is_same<R, float>::value) return v > 0.f ? v * rsqrtf(v) : 0.f;
+  else return sqrt(v);
+}
+
+// The correctly rounded square root in either precision: the summation
+// density, whose fused form in the neighbour filter uses the same root.
+template <typename R>
+__device__ __forceinline__ R sqrt_x(R v) {
   if constexpr (std::is_same<R, float>::value) return sqrtf(v);
   else return sqrt(v);
 }
