@@ -237,13 +237,17 @@ int sisph_set(sisph_t s, int32_t field, const double *in);
 
 /* Several fields in one call: fields[k] from in[k] / into out[k] (host
  * arrays of n doubles each, caller's order), the same as nfields calls of
- * sisph_set / sisph_get, but the copies and reorderings go out back to back
- * on the handle's stream, the FP32 mirrors are refreshed once after all
- * writes, and the call waits once.  Host arrays in page-locked memory copy
- * asynchronously.  Every field is checked before anything is copied: an
- * unknown or read-only field (or a third component in 2D) returns
- * SISPH_EINVAL with nothing written.  A step's whole state (positions,
- * velocities, transport velocities, pressure) moves in and out this way. */
+ * sisph_set / sisph_get, but each field has a device staging column of its
+ * own and its host copy runs on a copy stream of the handle, overlapping the
+ * reordering of the neighbouring field on the handle's stream; the FP32
+ * mirrors are refreshed once after all writes, and the call returns when
+ * every copy is done.  The staging (nfields x n doubles) is allocated at
+ * the first call that needs it and kept until sisph_destroy.  Host arrays
+ * in page-locked memory copy asynchronously.  Every field is checked before
+ * anything is copied: an unknown or read-only field (or a third component
+ * in 2D) returns SISPH_EINVAL with nothing written.  A step's whole state
+ * (positions, velocities, transport velocities, pressure) moves in and out
+ * this way. */
 int sisph_set_many(sisph_t s, int32_t nfields, const int32_t *fields, const double *const *in);
 int sisph_get_many(sisph_t s, int32_t nfields, const int32_t *fields, double *const *out);
 

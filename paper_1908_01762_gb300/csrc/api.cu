@@ -82,6 +82,13 @@ struct sisph_s {
   int counting = 1;
   double *d_tmp = nullptr, *d_tmp2 = nullptr;
   long long sweep_units_pending = 0;
+  // sisph_get_many / sisph_set_many: one staging column of n doubles per
+  // field and a copy stream of their own, so that each field's host copy
+  // overlaps the reordering of the field before (or after) it
+  double *d_stage = nullptr;
+  int stage_fields = 0;
+  cudaStream_t copy = nullptr;
+  std::vector<cudaEvent_t> xev;
 };
 
 namespace {
@@ -968,6 +975,10 @@ void sisph_destroy(sisph_t s) {
   }
   for (auto ev : s->pool) cudaEventDestroy(ev);
   for (void *p : s->allocs) cudaFree(p);
+  if (s->copy) cudaStreamSynchronize(s->copy);
+  if (s->d_stage) cudaFree(s->d_stage);
+  for (auto ev : s->xev) cudaEventDestroy(ev);
+  if (s->copy) cudaStreamDestroy(s->copy);
   if (s->own_stream) cudaStreamDestroy(s->own_stream);
   if (s->side) cudaStreamDestroy(s->side);
   delete s;
@@ -1111,17 +1122,43 @@ static bool get_source(sisph_t s, int32_t field, const void **src) {
   }
 }
 
-// Scatter one field into caller order in d_tmp and queue its copy to out.
-static cudaError_t queue_get(sisph_t s, int32_t field, const void *src, double *out) {
+// Scatter one field into caller order in tmp (n doubles) on the library's
+// stream.
+static cudaError_t queue_scatter(sisph_t s, int32_t field, const void *src, double *tmp) {
   State &S = s->S;
   Launch L = mk_launch(s);
   L.before = nullptr;
   L.after = nullptr;
-  cudaError_t e;
-  if (field >= SISPH_F_DX && field <= SISPH_F_DZ) e = launch_scatter_disp(S, L, field - SISPH_F_DX, s->d_tmp);
-  else if (field == SISPH_F_NSKIN || field == SISPH_F_NCOUNT) e = launch_scatter_field(S, L, src, 2, 0, 0, s->d_tmp);
-  else e = launch_scatter_field(S, L, src, 0, 0, 0, s->d_tmp);
+  if (field >= SISPH_F_DX && field <= SISPH_F_DZ) return launch_scatter_disp(S, L, field - SISPH_F_DX, tmp);
+  if (field == SISPH_F_NSKIN || field == SISPH_F_NCOUNT) return launch_scatter_field(S, L, src, 2, 0, 0, tmp);
+  return launch_scatter_field(S, L, src, 0, 0, 0, tmp);
+}
+
+// Scatter one field into caller order in d_tmp and queue its copy to out.
+static cudaError_t queue_get(sisph_t s, int32_t field, const void *src, double *out) {
+  cudaError_t e = queue_scatter(s, field, src, s->d_tmp);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, s->d_tmp, size_t(s->n) * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  return e;
+}
+
+// Staging for nf fields (grown on demand; the previous call has finished
+// with it, since every get/set waits for its copies), the copy stream and
+// nf + 1 ordering events.
+static cudaError_t ensure_stage(sisph_t s, int nf) {
+  cudaError_t e = cudaSuccess;
+  if (!s->copy) e = cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking);
+  if (e == cudaSuccess && s->stage_fields < nf) {
+    if (s->d_stage) cudaFree(s->d_stage);
+    s->d_stage = nullptr;
+    s->stage_fields = 0;
+    e = cudaMalloc(&s->d_stage, size_t(nf) * size_t(s->n) * sizeof(double));
+    if (e == cudaSuccess) s->stage_fields = nf;
+  }
+  while (e == cudaSuccess && int(s->xev.size()) < nf + 1) {
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) s->xev.push_back(ev);
+  }
   return e;
 }
 
@@ -1143,8 +1180,19 @@ int sisph_get_many(sisph_t s, int32_t nfields, const int32_t *fields, double *co
     if (!out[k]) return fail(s, SISPH_EINVAL, "a NULL output array");
     if (!get_source(s, fields[k], &src[k])) return fail(s, SISPH_EINVAL, "unknown field");
   }
-  cudaError_t e = cudaSuccess;
-  for (int k = 0; k < nfields && e == cudaSuccess; ++k) e = queue_get(s, fields[k], src[k], out[k]);
+  // field k: scatter into its staging column on the library's stream, then
+  // its copy to the host on the copy stream, which waits for that scatter
+  // only, so the copy of field k overlaps the scatter of field k + 1
+  cudaError_t e = nfields > 0 ? ensure_stage(s, nfields) : cudaSuccess;
+  const size_t bytes = size_t(s->n) * sizeof(double);
+  for (int k = 0; k < nfields && e == cudaSuccess; ++k) {
+    double *st = s->d_stage + size_t(k) * size_t(s->n);
+    e = queue_scatter(s, fields[k], src[k], st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->xev[k], s->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->copy, s->xev[k], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out[k], st, bytes, cudaMemcpyDeviceToHost, s->copy);
+  }
+  if (e == cudaSuccess && nfields > 0) e = cudaStreamSynchronize(s->copy);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "get_many");
   return SISPH_OK;
@@ -1206,8 +1254,22 @@ int sisph_set_many(sisph_t s, int32_t nfields, const int32_t *fields, const doub
   Launch L = mk_launch(s);
   L.before = nullptr;
   L.after = nullptr;
-  cudaError_t e = cudaSuccess;
-  for (int k = 0; k < nfields && e == cudaSuccess; ++k) e = queue_set(s, fields[k], dst[k], in[k]);
+  // field k: its copy into its staging column on the copy stream (after the
+  // work already queued on the library's stream), then its gather into the
+  // sorted order on the library's stream, which waits for that copy only, so
+  // the gather of field k overlaps the copy of field k + 1
+  cudaError_t e = nfields > 0 ? ensure_stage(s, nfields) : cudaSuccess;
+  const size_t bytes = size_t(s->n) * sizeof(double);
+  if (e == cudaSuccess && nfields > 0) e = cudaEventRecord(s->xev[nfields], s->stream);
+  if (e == cudaSuccess && nfields > 0) e = cudaStreamWaitEvent(s->copy, s->xev[nfields], 0);
+  for (int k = 0; k < nfields && e == cudaSuccess; ++k) {
+    double *st = s->d_stage + size_t(k) * size_t(s->n);
+    e = cudaMemcpyAsync(st, in[k], bytes, cudaMemcpyHostToDevice, s->copy);
+    if (e == cudaSuccess) e = cudaEventRecord(s->xev[k], s->copy);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->xev[k], 0);
+    // positions: a wall that moved forces every case to be rebuilt
+    if (e == cudaSuccess) e = launch_gather_field(s->S, L, st, dst[k], fields[k] <= SISPH_F_Z);
+  }
   if (e == cudaSuccess && nfields > 0) e = launch_refresh_mirrors(s->S, L);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "set_many");

@@ -68,3 +68,21 @@ def test_many_rejects_a_bad_field_before_writing(sisph):
     with pytest.raises(sisph.SisphError):
         sim.get_many(["p", 999])
     sim.close()
+
+
+def test_many_grows_its_staging_between_calls(sisph):
+    """A first call with one field, then calls with more: the staging grows
+    and every field still matches its single-field read."""
+    case = workloads.dam_break_2d(dx=0.04)
+    sim = sisph.Simulation(case, precision=sisph.MIXED)
+    sim.step(2)
+    (p,) = sim.get_many(["p"])
+    assert np.array_equal(p, sim.get("p"))
+    fields = STATE[2] + ["rho", "ncount", "nx", "ny"]
+    for f, g in zip(fields, sim.get_many(fields)):
+        assert np.array_equal(g, sim.get(f)), f
+    new = [sim.get(f) + (1e-3 if f in ("u", "v") else 0.0) for f in STATE[2]]
+    sim.set_many(STATE[2], new)
+    for f, v in zip(STATE[2], new):
+        assert np.array_equal(sim.get(f), v), f
+    sim.close()
