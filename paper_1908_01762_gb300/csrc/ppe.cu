@@ -589,7 +589,7 @@ __device__ __forceinline__ bool sweep_tail(const State &S, const int *apre, int 
   return true;
 }
 
-template <bool MX, int CH>
+template <bool MX, int CH, bool TAIL>
 __global__ void __launch_bounds__(256, sweep_blocks_per_sm(MX, CH)) k_sweeps(State S) {
   using R = SweepReal<MX>;
   __shared__ double sh[64];
@@ -662,7 +662,7 @@ __global__ void __launch_bounds__(256, sweep_blocks_per_sm(MX, CH)) k_sweeps(Sta
     }) : S.nft;
     // fewer tiles than blocks: the tail (every block takes the same branch,
     // since all read the same stop counts after the grid barrier)
-    if (bal && ntiles < int(nb)) {
+    if (TAIL && bal && ntiles < int(nb)) {
       alive = sweep_tail<MX, CH>(S, apre, ntiles, k, kcap, skip, sh, &flag);
       tail = true;
       break;
@@ -1044,9 +1044,14 @@ cudaError_t launch_ppe_setup(const State &S, const Launch &L) {
 
 // The barrier-form kernel for the state's precision and dimension.
 using SweepKernel = void (*)(State);
+// The tail is compiled in for batches only: a single case's grid is sized to
+// its own tiles, so a per-case barrier would be its grid barrier, and the
+// tail's code costs the 3D kernel about 1 % of its sweep time.
 SweepKernel sweep_kernel(const State &S) {
-  if (!S.mixed) return k_sweeps<false, 8>;
-  return S.dim == 3 ? k_sweeps<true, 16> : k_sweeps<true, 12>;
+  const bool tail = S.ncases > 1;
+  if (!S.mixed) return tail ? k_sweeps<false, 8, true> : k_sweeps<false, 8, false>;
+  if (S.dim == 3) return tail ? k_sweeps<true, 16, true> : k_sweeps<true, 16, false>;
+  return tail ? k_sweeps<true, 12, true> : k_sweeps<true, 12, false>;
 }
 
 int ppe_max_blocks_per_sm(const State &S, int block, bool p2p) {
