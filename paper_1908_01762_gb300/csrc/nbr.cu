@@ -610,7 +610,7 @@ struct PeriodicBox {
 template <int DIM, bool EXACT, bool DENS = false>
 __global__ void __launch_bounds__(256, 4) k_filter(State S) {
   constexpr int kBand = DIM == 3 ? 48 : 16;   // at most 64 (one bit each below)
-  constexpr int kU = DIM == 3 ? 4 : 8;         // candidates whose loads go out together
+  constexpr int kU = DIM == 3 ? 4 : 6;         // candidates whose loads go out together
   const Tile &t = tile_of(S, blockIdx.x);
   const int i = t.beg + threadIdx.x;
   if (i >= t.end) return;
@@ -638,10 +638,19 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
   const bool dens = DENS && blockIdx.x < unsigned(S.nft);
   const float dih = float(P.inv_h);
   float rho = 0.f;
-  // a kept pair of a fluid row: its list entry and, with DENS, m_j W_ij
-  auto keep = [&](unsigned entry, float r2f, float mj) {
-    append(entry);
-    if (DENS && dens) rho += mj * poly_w<float>(sqrtf(r2f) * dih);
+  // a candidate of the skin list, kept or not (k), without a branch: a kept
+  // entry is stored while the row has room and, with DENS, adds m_j W_ij to
+  // the density; one not kept adds 0.  (Under a branch the warp would run
+  // the kept path whenever one lane keeps, which is almost always, and pay
+  // for the branch on top.)
+  auto keep_if = [&](bool k, unsigned entry, float r2f, float mj) {
+    if (k && cnt < S.cap) S.nbr[ell_at(S.cap, cnt, i)] = entry;
+    over = over || (k && cnt >= S.cap);
+    cnt += k ? 1 : 0;
+    if (DENS && dens) {
+      const float w = mj * poly_w<float>(sqrtf(r2f) * dih);
+      rho += k ? w : 0.f;
+    }
   };
   auto exact = [&](unsigned entry) {
     const double xi[3] = {S.x[0][i], S.x[1][i], DIM == 3 ? S.x[2][i] : 0.0};
@@ -677,19 +686,19 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
       en[u] = q < scnt ? S.snbr[sb + (long long)q * kEllBlock] : self;
     }
     _Pragma("unroll") for (int u = 0; u < kU; ++u) {
-      if (q0 + u >= scnt) continue;
+      const bool valid = q0 + u < scnt;
       float d[3];
       const float r2f = pair_f<DIM>(lc, pi, pj[u], e[u] >> kCodeShift, d);
       const bool near = own_near && near_cell<DIM>(pj[u], lc);
-      if (near && r2f < lo_band) {
-        keep(e[u], r2f, pj[u].w);
-      } else if (!near) {
+      bool k = valid && near && r2f < lo_band;
+      // rare: a particle outside the near range, or (exact rows) a pair in
+      // the band around the cutoff: set aside for the FP64 test after the
+      // loop, or decided here by it (not exact rows, or a full band)
+      if (valid && (!near || (ex && r2f >= lo_band && r2f <= hi_band))) {
         if (ex && nband < kBand) band[nband++] = e[u];
-        else if (exact(e[u])) keep(e[u], r2f, pj[u].w);
-      } else if (ex && r2f <= hi_band) {
-        if (nband < kBand) band[nband++] = e[u];
-        else if (exact(e[u])) append(e[u]);     // a full band: decided here
+        else k = exact(e[u]);
       }
+      keep_if(k, e[u], r2f, pj[u].w);
     }
   }
   if (ex && nband) {
