@@ -433,6 +433,13 @@ __global__ void __launch_bounds__(256) k_skin(State S) {
     else over = true;
     ++cnt;
   };
+  // the same for a candidate that is kept or not (k), without a branch
+  auto append_if = [&](bool k, unsigned entry) {
+    k = k && (wall_row || (entry & kIdxMask) != unsigned(i));
+    if (k && cnt < S.scap) S.snbr[ell_at(S.scap, cnt, i)] = entry;
+    over = over || (k && cnt >= S.scap);
+    cnt += k ? 1 : 0;
+  };
   // candidates of the stencil cells in buckets k0..k1 (0 fluid, 1 walls);
   // exact: N(i) itself (3h, walls only), else the skin test (3h + s)
   auto scan = [&](int k0, int k1, bool exact) {
@@ -478,18 +485,15 @@ __global__ void __launch_bounds__(256) k_skin(State S) {
               continue;
             }
             // candidates 8 at a time: the loads go out together; slots past
-            // the cell's end get a far-away position and are rejected below
+            // the cell's end get a position inside the near range, four cells
+            // away, and are rejected by their index
             for (unsigned j0 = beg; j0 < end; j0 += 8) {
               float4 pj[8];
               _Pragma("unroll") for (int u = 0; u < 8; ++u)
-                pj[u] = j0 + u < end ? S.pf4[j0 + u] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
+                pj[u] = j0 + u < end ? S.pf4[j0 + u] : make_float4(4.f * lx, 4.f * ly, 4.f * lz, 0.f);
               _Pragma("unroll") for (int u = 0; u < 8; ++u) {
                 const unsigned j = j0 + u;
-                if (!near_cell<DIM>(pj[u], lc)) {
-                  double d[3];
-                  if (j < end && pair_d<DIM>(P, xi, S.xref, int(j), d) < cut_d) append(j | code);
-                  continue;
-                }
+                const bool nr = near_cell<DIM>(pj[u], lc);
                 float dx = fx - pj[u].x, dy = fy - pj[u].y;
                 float r2f = dx * dx + dy * dy;
                 if (DIM == 3) {
@@ -497,7 +501,17 @@ __global__ void __launch_bounds__(256) k_skin(State S) {
                   r2f += dz * dz;
                 }
                 if (!exact) {
-                  if (r2f < cut2f) append(j | code);
+                  // the common case without a branch; a particle outside
+                  // the near range (rare) takes the FP64 test
+                  bool k = nr && r2f < cut2f && j < end;
+                  if (!nr) {
+                    double d[3];
+                    k = j < end && pair_d<DIM>(P, xi, S.xref, int(j), d) < cut_d;
+                  }
+                  append_if(k, j | code);
+                } else if (!nr) {
+                  double d[3];
+                  if (j < end && pair_d<DIM>(P, xi, S.xref, int(j), d) < cut_d) append(j | code);
                 } else if (r2f < lo_band) {
                   append(j | code);
                 } else if (r2f <= hi_band) {
