@@ -640,13 +640,13 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
   const int scnt = S.sncnt[i];
   const int head = S.wfin[i];
   const long long sb = ell_base(S.scap, i);
+  // cnt counts every kept entry; one past the capacity is reported after
+  // the loops
   int cnt = 0;
-  bool over = false;
   unsigned band[kBand];
   int nband = 0;
   auto append = [&](unsigned entry) {
     if (cnt < S.cap) S.nbr[ell_at(S.cap, cnt, i)] = entry;
-    else over = true;
     ++cnt;
   };
   const bool dens = DENS && blockIdx.x < unsigned(S.nft);
@@ -659,7 +659,6 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
   // for the branch on top.)
   auto keep_if = [&](bool k, unsigned entry, float r2f, float mj) {
     if (k && cnt < S.cap) S.nbr[ell_at(S.cap, cnt, i)] = entry;
-    over = over || (k && cnt >= S.cap);
     cnt += k ? 1 : 0;
     if (DENS && dens) {
       const float w = mj * poly_w<float>(sqrtf(r2f) * dih);
@@ -682,39 +681,47 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
     }
   }
   // the next chunk's entries are loaded while this chunk's positions are
-  // gathered (a slot past the row's end reads the row itself)
+  // gathered (a slot past the row's end reads the row itself).  The loop is
+  // compiled twice, for exact rows and for the others (a block-uniform
+  // choice), so that the others test only for a particle outside the near
+  // range
   const unsigned self = unsigned(i) | (stencil_code(0, 0, 0) << kCodeShift);
-  unsigned en[kU];
-  _Pragma("unroll") for (int u = 0; u < kU; ++u)
-    en[u] = head + u < scnt ? S.snbr[sb + (long long)(head + u) * kEllBlock] : self;
-  for (int q0 = head; q0 < scnt; q0 += kU) {
-    unsigned e[kU];
-    float4 pj[kU];
-    _Pragma("unroll") for (int u = 0; u < kU; ++u) {
-      e[u] = en[u];
-      SISPH_CHECK_ENTRY(S, e[u], self);
-      pj[u] = S.pf4[e[u] & kIdxMask];
-    }
-    _Pragma("unroll") for (int u = 0; u < kU; ++u) {
-      const int q = q0 + kU + u;
-      en[u] = q < scnt ? S.snbr[sb + (long long)q * kEllBlock] : self;
-    }
-    _Pragma("unroll") for (int u = 0; u < kU; ++u) {
-      const bool valid = q0 + u < scnt;
-      float d[3];
-      const float r2f = pair_f<DIM>(lc, pi, pj[u], e[u] >> kCodeShift, d);
-      const bool near = own_near && near_cell<DIM>(pj[u], lc);
-      bool k = valid && near && r2f < lo_band;
-      // rare: a particle outside the near range, or (exact rows) a pair in
-      // the band around the cutoff: set aside for the FP64 test after the
-      // loop, or decided here by it (not exact rows, or a full band)
-      if (valid && (!near || (ex && r2f >= lo_band && r2f <= hi_band))) {
-        if (ex && nband < kBand) band[nband++] = e[u];
-        else k = exact(e[u]);
+  auto candidates = [&](auto exact_rows) {
+    constexpr bool EX = decltype(exact_rows)::value;
+    unsigned en[kU];
+    _Pragma("unroll") for (int u = 0; u < kU; ++u)
+      en[u] = head + u < scnt ? S.snbr[sb + (long long)(head + u) * kEllBlock] : self;
+    for (int q0 = head; q0 < scnt; q0 += kU) {
+      unsigned e[kU];
+      float4 pj[kU];
+      _Pragma("unroll") for (int u = 0; u < kU; ++u) {
+        e[u] = en[u];
+        SISPH_CHECK_ENTRY(S, e[u], self);
+        pj[u] = S.pf4[e[u] & kIdxMask];
       }
-      keep_if(k, e[u], r2f, pj[u].w);
+      _Pragma("unroll") for (int u = 0; u < kU; ++u) {
+        const int q = q0 + kU + u;
+        en[u] = q < scnt ? S.snbr[sb + (long long)q * kEllBlock] : self;
+      }
+      _Pragma("unroll") for (int u = 0; u < kU; ++u) {
+        const bool valid = q0 + u < scnt;
+        float d[3];
+        const float r2f = pair_f<DIM>(lc, pi, pj[u], e[u] >> kCodeShift, d);
+        const bool near = own_near && near_cell<DIM>(pj[u], lc);
+        bool k = valid && near && r2f < lo_band;
+        // rare: a particle outside the near range, or (exact rows) a pair in
+        // the band around the cutoff: set aside for the FP64 test after the
+        // loop, or decided here by it (not exact rows, or a full band)
+        if (valid && (!near || (EX && r2f >= lo_band && r2f <= hi_band))) {
+          if (EX && nband < kBand) band[nband++] = e[u];
+          else k = exact(e[u]);
+        }
+        keep_if(k, e[u], r2f, pj[u].w);
+      }
     }
-  }
+  };
+  if (ex) candidates(std::true_type{});
+  else candidates(std::false_type{});
   if (ex && nband) {
     PeriodicBox B;
     _Pragma("unroll") for (int k = 0; k < 3; ++k) {
@@ -733,7 +740,7 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
     for (int b = 0; b < nband; ++b)
       if ((keep >> b) & 1ull) append(band[b]);
   }
-  if (over) {
+  if (cnt > S.cap) {
     atomicOr(S.err, kErrCapacity);
     cnt = S.cap;
   }
