@@ -229,7 +229,6 @@ __global__ void k_stage1(State S) {
   G.init(S, i);
   const R nu4 = R(4.0 * P.nu), eh2 = R(P.eh2);
   const R avc = R(2.0 * P.alpha * P.h * P.c0);     // 2 alpha h c
-  const bool av = P.alpha > 0.0;
   const int fend = P.fbeg + P.nf;
   R ui[3], uti[3];
   vel<DIM, MX>(S, i, ui);
@@ -239,6 +238,10 @@ __global__ void k_stage1(State S) {
   R dti[3];
   _Pragma("unroll") for (int k = 0; k < 3; ++k) dti[k] = uti[k] - ui[k];
   R f[3] = {R(0), R(0), R(0)};
+  // the row loop is compiled with and without the artificial viscosity (a
+  // per-case choice), so that neither carries the other's branch
+  auto rows = [&](auto with_av) {
+  constexpr bool av = decltype(with_av)::value;
   ROW_CHUNKS(S, i, {
     int j;
     R d[3];
@@ -275,6 +278,9 @@ __global__ void k_stage1(State S) {
         f[k] += visc * uij[k] + coef * fr * d[k] + ui[k] * ai + uj[k] * aj;
     }
   })
+  };
+  if (P.alpha > 0.0) rows(std::true_type{});
+  else rows(std::false_type{});
   const double dt = P.dt;
   _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
     double fk = double(f[k]) + P.g[k];
@@ -466,8 +472,11 @@ __global__ void __launch_bounds__(256, 5) k_pgrad_gtvf1(State S) {
   const float pi = S.pf[i];
   const float pri = divr(pi, ri * ri);
   const float iri = 1.f / ri;
-  const bool symm = P.pgrad_symm != 0;
   float f[3] = {0.f, 0.f, 0.f}, acc[3] = {0.f, 0.f, 0.f};
+  // the row loop is compiled for each gradient form and with or without the
+  // GTVF sum (per-case choices), so that no pair carries their branches
+  auto rows = [&](auto symm_form, auto with_gtvf) {
+  constexpr bool symm = decltype(symm_form)::value, fused = decltype(with_gtvf)::value;
   ROW_CHUNKS(S, i, {
     const int j = int(e & kIdxMask);
     if (valid && j != i) {
@@ -487,6 +496,14 @@ __global__ void __launch_bounds__(256, 5) k_pgrad_gtvf1(State S) {
       }
     }
   })
+  };
+  if (P.pgrad_symm != 0) {
+    if (fused) rows(std::true_type{}, std::true_type{});
+    else rows(std::true_type{}, std::false_type{});
+  } else {
+    if (fused) rows(std::false_type{}, std::true_type{});
+    else rows(std::false_type{}, std::false_type{});
+  }
   const double dt = P.dt;
   double unew[3] = {0, 0, 0};
   _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
