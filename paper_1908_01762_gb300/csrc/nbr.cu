@@ -653,14 +653,15 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
   const float dih = float(P.inv_h);
   float rho = 0.f;
   // a candidate of the skin list, kept or not (k), without a branch: a kept
-  // entry is stored while the row has room and, with DENS, adds m_j W_ij to
-  // the density; one not kept adds 0.  (Under a branch the warp would run
-  // the kept path whenever one lane keeps, which is almost always, and pay
-  // for the branch on top.)
-  auto keep_if = [&](bool k, unsigned entry, float r2f, float mj) {
+  // entry is stored while the row has room and, when the row sums its
+  // density (sum, a compile-time flag of each loop), adds m_j W_ij to it; one
+  // not kept adds 0.  (Under a branch the warp would run the kept path
+  // whenever one lane keeps, which is almost always, and pay for the branch
+  // on top.)
+  auto keep_if = [&](auto sum, bool k, unsigned entry, float r2f, float mj) {
     if (k && cnt < S.cap) S.nbr[ell_at(S.cap, cnt, i)] = entry;
     cnt += k ? 1 : 0;
-    if (DENS && dens) {
+    if constexpr (decltype(sum)::value) {
       const float w = mj * poly_w<float>(sqrtf(r2f) * dih);
       rho += k ? w : 0.f;
     }
@@ -716,7 +717,8 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
           if (EX && nband < kBand) band[nband++] = e[u];
           else k = exact(e[u]);
         }
-        keep_if(k, e[u], r2f, pj[u].w);
+        // exact rows are wall rows or the API's lists: neither sums a density
+        keep_if(std::integral_constant<bool, DENS && !EX>{}, k, e[u], r2f, pj[u].w);
       }
     }
   };

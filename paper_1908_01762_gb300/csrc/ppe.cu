@@ -110,6 +110,10 @@ __global__ void __launch_bounds__(256, MX ? 4 : 2) k_setup_fluid(State S) {
     // leave its zero coefficient out of the packed slots: entry k goes to
     // slot k - 1; other rows keep one slot per entry
     const int shift = (MX && (S.nbr[ell_at(S.cap, 0, i)] & kIdxMask) == unsigned(i)) ? 1 : 0;
+    // the row loop is compiled with and without the collection of tile
+    // dependencies (point-to-point form only)
+    auto rows = [&](auto p2p_form) {
+    constexpr bool P2P = decltype(p2p_form)::value;
     ROW_CHUNKS(S, i, {
       const int k = _q0 + _u;
       int j = int(e & kIdxMask);
@@ -148,12 +152,15 @@ __global__ void __launch_bounds__(256, MX ? 4 : 2) k_setup_fluid(State S) {
       if (valid && k >= shift)
         store_coef<R>(S.coef, slot_at(S, k - shift, i), j, fac);
       if (valid) {
-        if (S.p2p && j != i) {
+        if (P2P && j != i) {
           const int dt = S.tile_of[j];
           if (dt != int(blockIdx.x)) deps.insert(dt);
         }
       }
     })
+    };
+    if (S.p2p) rows(std::true_type{});
+    else rows(std::false_type{});
     S.pcnt[i] = S.ncnt[i] - shift;
     bool fs = P.free_surface && (double(ri) / P.rho0 < S.fs_ratio);
     bool active = (dg != R(0)) && !fs;
