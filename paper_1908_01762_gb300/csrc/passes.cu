@@ -246,7 +246,11 @@ __global__ void k_stage1(State S) {
     int j;
     R d[3];
     R r2 = G.pair(S, P, K.lc, e, j, d);
-    if (valid && j != i) {
+    // 3D: every slot runs the pair arithmetic and its contribution is masked
+    // (the row itself and the padding add 0), without a branch; 2D rows keep
+    // the branches, which measured faster there
+    const bool on = valid && j != i;
+    if (DIM == 3 || on) {
       R r = sqrt_r(r2);
       R dw = K.dsc * poly_dw<R>(qof<R>(r, K.h, K.ih));
       R fr = r > R(0) ? divr(dw, r) : R(0);
@@ -260,10 +264,23 @@ __global__ void k_stage1(State S) {
       if (av) {
         R vr = uij[0] * d[0] + uij[1] * d[1] + (DIM == 3 ? uij[2] * d[2] : R(0));
         // -m_j Pi_ij = m_j alpha h c phi_ij / ((rho_i + rho_j)/2)
-        if (vr < R(0)) coef = divr(mj * avc * vr, reta * rsum);
+        if constexpr (DIM == 3) coef = vr < R(0) ? divr(mj * avc * vr, reta * rsum) : R(0);
+        else if (vr < R(0)) coef = divr(mj * avc * vr, reta * rsum);
       }
       R ai = R(0), aj = R(0);
-      if (j < fend) {
+      if constexpr (DIM == 3) {
+        // the transport-velocity terms of fluid neighbours, masked for walls
+        const bool fl = j < fend;
+        R utj[3];
+        tvel<DIM, MX>(S, j, utj);
+        R gi = R(0), gj = R(0);
+        _Pragma("unroll") for (int k = 0; k < DIM; ++k) {
+          gi += dti[k] * d[k];
+          gj += (utj[k] - uj[k]) * d[k];
+        }
+        ai = fl ? mj * fr * gi * iri : R(0);
+        aj = fl ? divr(mj * fr * gj, rj) : R(0);
+      } else if (j < fend) {
         R utj[3];
         tvel<DIM, MX>(S, j, utj);
         R gi = R(0), gj = R(0);
@@ -275,7 +292,7 @@ __global__ void k_stage1(State S) {
         aj = divr(mj * fr * gj, rj);
       }
       _Pragma("unroll") for (int k = 0; k < DIM; ++k)
-        f[k] += visc * uij[k] + coef * fr * d[k] + ui[k] * ai + uj[k] * aj;
+        f[k] += on ? visc * uij[k] + coef * fr * d[k] + ui[k] * ai + uj[k] * aj : R(0);
     }
   })
   };

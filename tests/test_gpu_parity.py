@@ -338,6 +338,30 @@ def test_sweep_sync_forms_agree_with_an_empty_case(sisph):
     assert res[0][1] == res[1][1]
 
 
+def test_sweep_sync_forms_agree_when_a_case_stops_at_max_iter(sisph):
+    """A batch whose cavity cannot reach its tolerance: the vortex stops
+    after its 2 sweeps, so the barrier form finishes the cavity in its
+    per-case tail, where it stops at max_iter (SISPH_ENOTCONVERGED, which a
+    step reports and carries on from); both sync forms give the same bits
+    and the same sweep counts."""
+    def cases():
+        cav = workloads.lid_driven_cavity(30)
+        cav["params"]["tol"] = 1e-14
+        cav["params"]["max_iter"] = 7
+        return [workloads.taylor_green(24, tol=1e-2), cav, workloads.dam_break_2d(dx=0.05)]
+    res = []
+    for sync in (2, 1):
+        sim = sisph.Simulation(cases(), ppe_sync=sync)
+        sim.step(2)
+        st = sim.stats()
+        res.append((sim.get("p"), sim.get("u"), [(s.iters, s.total_iters, s.status) for s in st]))
+        sim.close()
+    assert res[0][2] == res[1][2]
+    assert res[1][2][1][0] == 7 and res[1][2][1][2] == sisph.ENOTCONVERGED
+    assert np.array_equal(res[0][0], res[1][0])
+    assert np.array_equal(res[0][1], res[1][1])
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_graph_replay_equals_direct(sisph, prec):
     case = workloads.lid_driven_cavity(24)
