@@ -118,7 +118,10 @@ __global__ void __launch_bounds__(256, MX ? 4 : 2) k_setup_fluid(State S) {
       const int k = _q0 + _u;
       int j = int(e & kIdxMask);
       R fac = R(0);
-      if (j != i) {
+      // 3D: the row itself and the padding run the pair arithmetic too and
+      // add nothing (no branch); 2D rows keep the branch
+      const bool on = j != i;
+      if (DIM == 3 || on) {
         R d[3], r2, rj, mj, uj[3];
         if constexpr (MX) {
           float4 pj = S.pf4[j];
@@ -140,10 +143,12 @@ __global__ void __launch_bounds__(256, MX ? 4 : 2) k_setup_fluid(State S) {
         _Pragma("unroll") for (int q = 0; q < DIM; ++q) ud += (ui[q] - uj[q]) * d[q];
         R src = -divr(mj * idt * fr * ud, rj);
         fac = divr(four_iri * mj * (fr * r2), (ri + rj) * (r2 + eh2));
-        if (!valid) { src = R(0); fac = R(0); }
+        if (!valid || !on) { src = R(0); fac = R(0); }
         if constexpr (MX) {
-          kahan_add(rhs, rc, src);
-          kahan_add(dg, dc, fac);
+          if (on) {          // a compensated sum must not see the extra zeros
+            kahan_add(rhs, rc, src);
+            kahan_add(dg, dc, fac);
+          }
         } else {
           rhs += src;
           dg += fac;
