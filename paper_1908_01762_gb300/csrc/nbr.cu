@@ -101,7 +101,9 @@ __device__ __forceinline__ bool near_cell(const float4 &p, const float lc[3]) {
 // FP32 position relative to the origin of the particle's rebuild cell (the
 // minimum image of it in periodic directions, since a particle may have
 // wrapped since the rebuild), and its mass: the neighbour tests use it, and
-// so do all MIXED neighbour sums.
+// so do all MIXED neighbour sums.  The mass carries the near-range test in
+// its sign (negative: outside the near range), so that a neighbour test
+// reads it with one comparison; every sum takes its magnitude.
 template <int DIM>
 __device__ __forceinline__ float4 rel_pos(const CaseDev &P, const double xi[3], long long cell, double m) {
   int c[3];
@@ -115,8 +117,13 @@ __device__ __forceinline__ float4 rel_pos(const CaseDev &P, const double xi[3], 
     }
     rel[k] = float(d);
   }
-  return make_float4(rel[0], rel[1], rel[2], float(m));
+  const float4 p = make_float4(rel[0], rel[1], rel[2], float(m));
+  const float lc[3] = {P.lcf[0], P.lcf[1], P.lcf[2]};
+  return make_float4(p.x, p.y, p.z, near_cell<DIM>(p, lc) ? p.w : -p.w);
 }
+
+// The near-range test of a mirrored position (the sign of its mass).
+__device__ __forceinline__ bool is_near(const float4 &p) { return p.w > 0.f; }
 
 // ---------------------------------------------------------------------------
 // check
@@ -631,7 +638,7 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
   const CaseDev &P = S.cases[t.c];
   const float4 pi = S.pf4[i];
   const float lc[3] = {P.lcf[0], P.lcf[1], P.lcf[2]};
-  const bool own_near = near_cell<DIM>(pi, lc);
+  const bool own_near = is_near(pi);
   const float cut2f = float(P.cut2);
   // wall rows stay exact: their Shepard sums are normalised, so a wall whose
   // only fluid neighbour sits on the rim takes that neighbour's value
@@ -708,7 +715,7 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
         const bool valid = q0 + u < scnt;
         float d[3];
         const float r2f = pair_f<DIM>(lc, pi, pj[u], e[u] >> kCodeShift, d);
-        const bool near = own_near && near_cell<DIM>(pj[u], lc);
+        const bool near = own_near && is_near(pj[u]);
         bool k = valid && near && r2f < lo_band;
         // rare: a particle outside the near range, or (exact rows) a pair in
         // the band around the cutoff: set aside for the FP64 test after the
@@ -718,7 +725,7 @@ __global__ void __launch_bounds__(256, 4) k_filter(State S) {
           else k = exact(e[u]);
         }
         // exact rows are wall rows or the API's lists: neither sums a density
-        keep_if(std::integral_constant<bool, DENS && !EX>{}, k, e[u], r2f, pj[u].w);
+        keep_if(std::integral_constant<bool, DENS && !EX>{}, k, e[u], r2f, fabsf(pj[u].w));
       }
     }
   };

@@ -39,7 +39,7 @@ struct Geo {
 
 template <bool MX>
 __device__ __forceinline__ auto mass(const State &S, int j) {
-  if constexpr (MX) return S.pf4[j].w;
+  if constexpr (MX) return fabsf(S.pf4[j].w);    // the sign holds the near-range test
   else return S.m[j];
 }
 template <bool MX>
@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(256, 5) k_pgrad_gtvf1(State S) {
       float d[3];
       float r2 = pair_f<DIM>(K.lc, pi4, pj4, e >> kCodeShift, d);
       float r = sqrt_r(r2);
-      float rj = S.vf4[j].w, mj = pj4.w, pj = S.pf[j];
+      float rj = S.vf4[j].w, mj = fabsf(pj4.w), pj = S.pf[j];
       float fr = r > 0.f ? divr(K.dsc * poly_dw<float>(qof<float>(r, K.h, K.ih)), r) : 0.f;
       float c = symm ? -mj * (pri + divr(pj, rj * rj)) : -divr(mj * (pj - pi), rj) * iri;
       c *= fr;

@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(256, MX ? 4 : 2) k_setup_fluid(State S) {
           r2 = pair_f<DIM>(K.lc, pi4, pj, e >> kCodeShift, d);
           float4 v = S.vf4[j];
           rj = v.w; uj[0] = v.x; uj[1] = v.y; uj[2] = v.z;
-          mj = pj.w;
+          mj = fabsf(pj.w);      // the sign holds the near-range test
         } else {
           double dd[3];
           r2 = pair_d<DIM>(P, xi, S.x, j, dd);
