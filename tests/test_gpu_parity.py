@@ -101,6 +101,38 @@ def test_neighbors_of_particles_outside_the_box(sisph, dim):
     sim.close()
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_mixed_density_with_particles_outside_the_box(sisph, dim):
+    """Particles clamped out of a closed box are outside the near range, which
+    the FP32 mirror carries in the sign of the mass: the MIXED density (the
+    separate pass, and the one the step's first refresh sums in its filter)
+    still uses |m| and the exact pair set, and matches the oracle within the
+    MIXED bound (the far cluster's pair vectors are FP32 differences of
+    coordinates some 10 cells from their cell's origin)."""
+    case = workloads.dam_break_2d(dx=0.05) if dim == 2 else workloads.dam_break_3d(dx=0.06)
+    case = dict(case)
+    rng = np.random.Generator(np.random.PCG64(5))
+    fl = np.nonzero(case["kind"] == 0)[0]
+    pick = rng.choice(fl, 12, replace=False)
+    for key, k in (("x", 0), ("y", 1), ("z", 2))[:dim]:
+        a = case[key].copy()
+        a[pick[:6]] = case["hi"][k] + 0.05 * rng.uniform(0, 1, 6)   # outside, near the wall
+        a[pick[6:]] = case["hi"][k] + 3.0 + 0.02 * rng.uniform(0, 1, 6)   # over 8 cells out, together
+        case[key] = a
+    ref = oracle.Sim(case)
+    ref.density()
+    want = ref.get("rho")
+    fluid = case["kind"] == 0
+    a = sisph.Simulation(case, precision=sisph.MIXED)
+    a.density()
+    b = sisph.Simulation(case, precision=sisph.MIXED)
+    b.step(1)                       # the density of the step's first refresh
+    for got in (a.get("rho"), b.get("rho")):
+        assert np.max(np.abs(got[fluid] - want[fluid]) / want[fluid]) < 1e-4
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("name", ["tgv_perturbed", "ldc", "db2d", "db3d"])
 def test_density_and_normals_fp64(sisph, name):
     case = CASES[name]
