@@ -370,6 +370,31 @@ def test_sweep_sync_forms_agree_with_an_empty_case(sisph):
     assert res[0][1] == res[1][1]
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_sweep_sync_forms_agree_on_a_3d_batch(sisph, prec):
+    """Two 3D dam breaks in one handle, the second at a tight tolerance: once
+    the first stops, the barrier form finishes the second in its per-case
+    tail (the 3D batch kernel); both sync forms give the same bits and the
+    same sweep counts."""
+    def cases():
+        a = workloads.dam_break_3d(dx=0.07)
+        b = workloads.dam_break_3d(dx=0.06)
+        b["params"]["tol"] = 1e-5
+        return [a, b]
+    out = []
+    for sync in (2, 1):
+        sim = sisph.Simulation(cases(), precision=prec, ppe_sync=sync)
+        sim.step(2)
+        out.append(({f: sim.get(f) for f in ("x", "y", "z", "u", "v", "w", "p")},
+                    [(s.iters, s.total_iters) for s in sim.stats()]))
+        sim.close()
+    (a, ia), (b, ib) = out
+    assert ia == ib
+    assert ib[1][0] > ib[0][0]          # the tight case swept on alone
+    for f in a:
+        assert np.array_equal(a[f], b[f]), f
+
+
 def test_sweep_sync_forms_agree_when_a_case_stops_at_max_iter(sisph):
     """A batch whose cavity cannot reach its tolerance: the vortex stops
     after its 2 sweeps, so the barrier form finishes the cavity in its
